@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark: milliseconds per optimisation iteration of density-based inverse
+homogenization (6 periodic cell problems to relative residual 1e-5, C^H, objective,
+sensitivities, filter adjoint and OC update) on one GB300.
+
+One step = one optimisation iteration on a 512^3 cell (134.2M elements; bulk-modulus
+objective, volume fraction 0.3, density filter radius 2, warm-started solves), the
+configuration of the paper's headline 512^3 row. Inputs are synthetic (seeded
+blurred-noise inclusion field), far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--n 512]
+
+Under torchrun (N > 1) every rank solves its own cell (replicas, no collective on the
+data path); rank 0 prints one JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PAPER_512_BULK_MS = 38030.0      # paper, 512^3 bulk vf 0.3: 38.03 s per iteration (GTX 1080Ti)
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--objective", default="bulk", choices=["bulk", "shear", "poisson", "logpoisson"])
+    ap.add_argument("--vf", type=float, default=0.3)
+    ap.add_argument("--tol", type=float, default=1e-5)
+    ap.add_argument("--max-iters", type=int, default=1000)
+    ap.add_argument("--seed", type=int, default=5)
+    ap.add_argument("--sample-n", type=int, default=16, help="cell size of the oracle's CPU sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------------ distributed harness
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """Maximum of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline bookkeeping
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# Algorithmic work per launch of each finest-level kernel class, N = n^3 vertices, 6 cases.
+# Bytes: minimum DRAM traffic the operation implies; flops: arithmetic of the algorithm.
+def algorithmic_work(kc: str, n: int):
+    N = n ** 3
+    if kc == "fine_gs":          # one colour pass: E 4N, the other colours' u 63N, f_c and u_c 9N+9N
+        return 85 * N, (576 + 26 * 54 + 6 * 15 + 30) * 2 * N / 8
+    if kc == "fine_matvec":      # E 4N + p 72N + q 72N; 27 blocks from E (576 FMA) + 26 x 6 x 9 FMA + 468 sub
+        return 148 * N, ((576 + 26 * 54) * 2 + 26 * 18) * N
+    if kc == "fine_residual":    # E 4N + x 72N + b 72N + out 72N
+        return 220 * N, ((576 + 27 * 54) * 2) * N
+    if kc == "element":          # u 72N + E/rho 8N (+ out 4N); 6 x 576 + 21 x 24 FMA per element
+        return 80 * N, (6 * 576 + 21 * 24) * 2 * N
+    return None, None
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("fine.cu", "dev_common.cuh", "homo_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2301_08911_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kc: str, n: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled to n^3; None if the
+    kernel source changed since it was captured."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(kc)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e["dram_bytes_per_launch"] * (n ** 3) / (e["n"] ** 3)
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import oracle
+from synthetic import smoothed_threshold_density
+n, vf, kind, reps = {n}, {vf}, {kind!r}, {reps}
+rho = smoothed_threshold_density(n, vf, {seed}).astype(np.float64)
+times = []
+for it in range(reps):
+    t0 = time.perf_counter()
+    out = oracle.optimization_iteration(rho, n, vf, kind, iteration=it)
+    times.append(time.perf_counter() - t0)
+    rho = out["rho_new"]
+print(json.dumps({{"times_s": times}}))
+"""
+
+
+def oracle_sample(n: int, vf: float, kind: str, reps: int, seed: int):
+    """Time `reps` oracle iterations at n^3 in a fresh single-threaded process."""
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    code = _ORACLE_SNIPPET.format(root=ROOT, n=n, vf=vf, kind=kind, reps=reps, seed=seed)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError(p.stderr[-2000:])
+    return json.loads(p.stdout.strip().splitlines()[-1])["times_s"]
+
+
+def workload_name(args):
+    return (f"{args.n}^3 periodic hex8 cell, {args.objective} objective, volume fraction {args.vf}, "
+            f"6 load cases to rel-res {args.tol:g}, filter radius 2, OC move 0.05 damping 0.5, "
+            f"warm-started MG-PCG")
+
+
+def config_dict(args):
+    return {"workload": workload_name(args), "n": args.n, "elements": args.n ** 3,
+            "objective": args.objective, "volfrac": args.vf, "rel_tol": args.tol,
+            "density": f"seeded blurred-noise inclusions (seed {args.seed}), exactly vf solid",
+            "l2": "inputs larger than L2 (18 planes x n^3 fp32 per field)",
+            "parallelism": "replicas (one cell per GPU, no collective)"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    reps = args.warmup + args.steps
+    times = oracle_sample(args.sample_n, args.vf, args.objective, reps, args.seed)
+    timed = times[args.warmup:]
+    scale = (args.n ** 3) / (args.sample_n ** 3)
+    ms = 1000.0 * statistics.mean(timed) * scale
+    sample = (f"oracle (numpy/scipy FP64, sparse LU solve) optimisation iterations at "
+              f"{args.sample_n}^3, {args.steps} timed after {args.warmup} warm-up, scaled linearly by "
+              f"element count to {args.n}^3 (a lower bound: the direct solve grows faster than linearly)")
+    line = {"impl": "reference", "metric": "ms per optimization iteration", "value": ms, "unit": "ms",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(args),
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2301_08911_gb300 import binding
+    from synthetic import smoothed_threshold_density
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    rho0 = smoothed_threshold_density(n, args.vf, args.seed + rank)
+    stream = torch.cuda.current_stream(dev)
+    hom = binding.Homogenization(n, stream=stream.cuda_stream)
+    r = torch.from_numpy(rho0).to(dev)
+    rt = torch.empty_like(r)
+    s = torch.empty_like(r)
+    dc = torch.empty_like(r)
+    beta = 0.8
+    state = {"it": 0, "cg": [], "relres": []}
+
+    def step():
+        hom.filter(2.0, r, rt)
+        hom.set_density(rt)
+        its, rel, _ = hom.solve_cases(args.tol, args.max_iters, warm_start=True, raise_on_noconv=False)
+        C = hom.CH()
+        f, g = binding.objective(args.objective, C, state["it"], beta)
+        hom.sensitivity(g, s)
+        hom.filter(2.0, s, dc)
+        hom.update(dc, r, args.vf)
+        state["it"] += 1
+        state["cg"].append(its)
+        state["relres"].append(max(rel))
+        return f
+
+    # warm-up (the first one is the cold solve from zero displacement)
+    cold_ms = None
+    for w in range(args.warmup):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if w == 0:
+            cold_ms = e0.elapsed_time(e1)
+    state["cg"].clear()
+    state["relres"].clear()
+
+    # timed region
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    hom.profile(True)
+    launches0 = hom.launch_count
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    launches = hom.launch_count - launches0
+    prof = hom.profile_read()
+    hom.profile(False)
+    clocks = sampler.stop()
+    t_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    ms_step = t_ms / args.steps
+
+    # end to end through the public API with host buffers: pinned host density in, new
+    # density and C^H out, every step
+    e2e = None
+    if not args.no_e2e:
+        host_rho = torch.from_numpy(r.cpu().numpy()).pin_memory()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for _ in range(args.steps):
+            r.copy_(host_rho, non_blocking=True)
+            step()
+            host_rho.copy_(r, non_blocking=True)
+        h1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        te = max_over_ranks(h0.elapsed_time(h1), world)
+        e2e = {"value": te / args.steps, "unit": "ms", "h2d_bytes_per_step": 4 * n ** 3,
+               "d2h_bytes_per_step": 4 * n ** 3 + 36 * 8}
+
+    if rank != 0:
+        return 0
+
+    # dominant kernel and its roofline
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    kc, (kn, kms) = dom
+    peak_hbm, peak_src = measured_peaks()
+    nbytes, nflops = algorithmic_work(kc, n)
+    roofline = None
+    if nbytes is not None and kn > 0:
+        avg_s = kms / kn / 1000.0
+        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+        alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s FP32
+        t_hbm = nbytes / (peak_hbm * 1e9)
+        t_alu = nflops / (alu_peak * 1e12)
+        traffic = recorded_traffic(kc, n)
+        if t_hbm >= t_alu:
+            ach = nbytes / avg_s / 1e9
+            roofline = {"bound": "hbm", "kernel": kc, "achieved": ach, "peak": peak_hbm, "unit": "GB/s",
+                        "frac": ach / peak_hbm, "traffic": traffic, "peak_source": peak_src,
+                        "bytes_per_launch": nbytes, "avg_launch_ms": kms / kn}
+        else:
+            ach = nflops / avg_s / 1e12
+            roofline = {"bound": "alu", "kernel": kc, "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
+                        "frac": ach / alu_peak, "traffic": traffic,
+                        "peak_source": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz",
+                        "flops_per_launch": nflops, "bytes_per_launch": nbytes,
+                        "hbm_frac": nbytes / avg_s / 1e9 / peak_hbm, "avg_launch_ms": kms / kn}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        reps = 2
+        times = oracle_sample(args.sample_n, args.vf, args.objective, reps, args.seed)
+        scale = (n ** 3) / (args.sample_n ** 3)
+        cpu = {"value": 1000.0 * statistics.mean(times) * scale, "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": f"{reps} oracle iterations at {args.sample_n}^3 (FP64 numpy/scipy, sparse LU), "
+                         f"single thread, scaled linearly by element count to {n}^3 (lower bound)"}
+
+    cg = np.array(state["cg"])
+    line = {
+        "metric": "ms per optimization iteration (6 cases to rel-res 1e-5)",
+        "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": (ms_step / PAPER_512_BULK_MS) if (n == 512 and args.objective == "bulk"
+                                                          and abs(args.vf - 0.3) < 1e-9) else None,
+        "dtype": "f32", "data": "synthetic", "config": config_dict(args),
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "gpu_launches": launches,
+        "solver": {"cold_first_iteration_ms": cold_ms,
+                   "cg_iterations_per_step": cg.max(axis=1).tolist() if cg.size else [],
+                   "max_final_relres": max(state["relres"]) if state["relres"] else None},
+        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_setup()
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,251 @@
+/*
+ * homo.h - C ABI of a GB300 (sm_103a) solver for the per-iteration hot path of
+ * density-based inverse homogenization (Zhang et al., "An optimized, easy-to-use,
+ * open-source GPU solver for large-scale inverse homogenization problems",
+ * arXiv 2301.08911).
+ *
+ * One optimisation iteration (paper Sec. 3.3 "Solver for IHP", Sec. 5.2 main loop):
+ *   homo_filter (rho -> rho~)          Sec. 5.2 / Sec. 6.4 periodic density filter
+ *   homo_set_density (rho~ -> E)       SIMP, Sec. 3.2
+ *   homo_solve_cases                   6 periodic cell problems K u_i = f_i (Eq. 4-5),
+ *                                      multigrid-preconditioned CG (Sec. 3.3, Alg. 1)
+ *   homo_CH                            homogenised tensor C^H (Eq. 7)
+ *   homo_objective (host arithmetic)   f(C^H), df/dC^H (Eq. 19-22)
+ *   homo_sensitivity                   df/d rho~ (Eq. 8-9)
+ *   homo_filter (adjoint = itself)     df/d rho
+ *   homo_update                        OC volume-constrained update (Sec. 3.3)
+ *
+ * Grid and layout conventions (every entry point):
+ *   - n^3 voxel elements, periodic; n^3 vertices. Scalar element/vertex fields are
+ *     float arrays of length N = n^3 with x fastest: index = x + n*(y + n*z).
+ *   - Element local vertex j = a + 2b + 4c sits at offset (a,b,c) from the element
+ *     origin; element (x,y,z) owns vertices (x..x+1, y..y+1, z..z+1) mod n.
+ *   - Displacement / load fields of the 6 load cases are 18 planes of N floats:
+ *     plane (3*case + comp), case in Voigt order 11,22,33,12,23,13 (Sec. 3.2),
+ *     comp in x,y,z. Total 18*N floats.
+ *   - Units: the library works in voxel units (element side 1, |Omega| = N).
+ *     Against the paper's Omega = [0,1]^3 (h = 1/n): u_paper = h*u, f_paper = h^2*f,
+ *     K_paper = h*K. C^H and sensitivities are unit-free and equal to the paper's.
+ *
+ * Memory and ownership: a context owns every device buffer it needs (filtered
+ * density, moduli, the 6 displacement fields kept as warm starts, the multigrid
+ * hierarchy, scratch). Pointers passed in are only read/written inside the call, on
+ * the context's stream; "device" pointers must be device-accessible CUDA memory (for
+ * example torch tensors' data_ptr()), "host" pointers ordinary host memory.
+ *
+ * Errors: every int-returning call returns HOMO_OK (0) or one of the HOMO_E* codes
+ * below; no exception crosses the ABI. homo_last_error(ctx) returns a message for the
+ * last failing call on that context (homo_last_error(NULL): last homo_create failure
+ * on this thread). After HOMO_ECUDA the context should be destroyed.
+ *
+ * Threading: a context is not thread-safe; distinct contexts may be used from
+ * distinct threads.
+ */
+#ifndef HOMO_H
+#define HOMO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HOMO_OK 0
+#define HOMO_EINVAL 1      /* bad argument: size, pointer, parameter range            */
+#define HOMO_ENOMEM 2      /* device or pinned-host allocation failed                  */
+#define HOMO_ECUDA 3       /* a CUDA runtime call or kernel launch failed              */
+#define HOMO_ENOCONV 4     /* max iterations reached; outputs valid, residuals given   */
+#define HOMO_EDIVERGED 5   /* a residual norm became non-finite or blew up             */
+#define HOMO_ESTATE 6      /* call out of order (e.g. homo_CH before a solve)          */
+
+#define HOMO_NUM_CASES 6
+
+/* Objective kinds for homo_objective (Sec. 5.2-5.3). */
+#define HOMO_OBJ_BULK 0        /* Eq. 19: -(C00+C11+C22+2(C01+C02+C12))/9              */
+#define HOMO_OBJ_SHEAR 1       /* Eq. 20: -(C33+C44+C55)/3                              */
+#define HOMO_OBJ_POISSON 2     /* Eq. 21: C01+C02+C12 - beta^iter (C00+C11+C22)         */
+#define HOMO_OBJ_LOGPOISSON 3  /* Eq. 22: log(1+eta(C01+C12+C20)/(C00+C11+C22))
+                                            + tau (C00+C11+C22)^gamma, eta 0.6, gamma 0.5,
+                                            tau = -1/E0^gamma                             */
+
+typedef struct homo_ctx homo_ctx;
+
+/* Optional solver settings. Zero-initialise and set struct_size = sizeof(homo_opts);
+ * zero fields take the defaults. */
+typedef struct homo_opts {
+  int struct_size;
+  int min_coarse;   /* coarsen by 2 while the next level keeps >= min_coarse cells per
+                       axis (default 4, Sec. 3.3); the coarsest level is solved directly */
+  int max_levels;   /* cap on the number of levels, 0 = no cap                           */
+  int pre_sweeps;   /* 8-colour Gauss-Seidel sweeps before coarse correction (default 1) */
+  int post_sweeps;  /* sweeps after it, colours in reverse order (default 1)             */
+} homo_opts;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int homo_version(void);
+
+/* Static text for a status code. */
+const char* homo_status_string(int status);
+
+/* Create a context for an n^3 periodic cell (Sec. 3.1-3.2).
+ *   n     : cells per axis, 4 <= n <= 1024; every level that is smoothed must be even.
+ *   E0    : Young's modulus of the solid (> 0); nu: Poisson's ratio in (-1, 0.5).
+ *   p     : SIMP exponent (>= 1); Emin: floor modulus, 0 <= Emin < E0.
+ *           Element modulus E_e = Emin + rho~_e^p (E0 - Emin).
+ *   opts  : nullable.
+ * Allocates every device buffer up front (about 450 bytes per element for n = 512).
+ * Uses the current CUDA device. Returns HOMO_EINVAL / HOMO_ENOMEM / HOMO_ECUDA. */
+int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Emin,
+                const homo_opts* opts);
+
+/* Free every resource of the context (synchronises its stream). NULL is accepted. */
+int homo_destroy(homo_ctx* ctx);
+
+/* Last error message of the context, or of the last failed homo_create on this
+ * thread when ctx is NULL. Never NULL. */
+const char* homo_last_error(const homo_ctx* ctx);
+
+/* Run all further work of the context on this cudaStream_t (NULL = legacy default
+ * stream). */
+int homo_set_stream(homo_ctx* ctx, void* cuda_stream);
+
+/* Number of multigrid levels and cells per axis of level l (0 = finest). */
+int homo_num_levels(const homo_ctx* ctx);
+int homo_level_size(const homo_ctx* ctx, int level);
+
+/* Periodic linear-cone filter (Sec. 5.2 "conv", Sec. 6 radius 2, Sec. 6.4 periodic
+ * kernel): out_e = sum_d w(d) in_(e+d) / sum_d w(d), w(d) = max(0, radius - |d|), d
+ * integer offsets between element centres, wrapped periodically. The operator is
+ * symmetric, so the same call applies its adjoint to sensitivities.
+ *   in, out: device, N floats each; must not alias. 0 < radius <= 3.5. */
+int homo_filter(homo_ctx* ctx, double radius, const float* in, float* out);
+
+/* Set the physical (filtered) density rho~ and derive E_e (Sec. 3.2). Values are
+ * clamped to [0, 1]. rho: N floats, device (on_device = 1) or host (on_device = 0).
+ * Marks loads and the multigrid hierarchy stale; the 6 displacement fields are kept
+ * as warm starts (Sec. 4.1 "Different GPU memory types"). */
+int homo_set_density(homo_ctx* ctx, const float* rho, int on_device);
+
+/* Solve K(E) u_i = f_i for the 6 unit macro strains (Eq. 4-5, Eq. 11-12) with CG
+ * preconditioned by one multigrid V-cycle (Alg. 1): 8-colour block Gauss-Seidel
+ * (Eq. 13-16), trilinear transfers, Galerkin coarse levels (Eq. 17-18), a direct
+ * coarsest solve with the rigid-translation null space projected out (Sec. 4.2).
+ *   rel_tol   : stop case i when ||f_i - K u_i||_2 / ||f_i||_2 <= rel_tol (> 0).
+ *   max_iters : CG iteration cap (>= 1).
+ *   warm_start: 1 = start from the fields of the previous solve, 0 = from zero.
+ *   iters_out, relres_out: host arrays of 6 (nullable): CG iterations per case and
+ *               final true relative residual per case.
+ * Returns HOMO_ENOCONV if a case missed rel_tol within max_iters (fields valid),
+ * HOMO_EDIVERGED on a non-finite residual. Synchronises the stream. */
+int homo_solve_cases(homo_ctx* ctx, double rel_tol, int max_iters, int warm_start,
+                     int iters_out[6], double relres_out[6]);
+
+/* Homogenised tensor C^H_ij = (1/|Omega|) sum_e E_e (chi_i - u_i)_e^T K0 (chi_j - u_j)_e
+ * (Eq. 7) from the last solve. CH: host, 36 doubles, row-major 6x6, Voigt order
+ * 11,22,33,12,23,13, engineering shear. Synchronises the stream. */
+int homo_CH(homo_ctx* ctx, double CH[36]);
+
+/* Element sensitivities of an objective with gradient dfdCH (host, 36 doubles, each
+ * entry treated as an independent variable) with respect to the filtered density
+ * (Eq. 8-9; the sum over e printed in Eq. 9 read as a per-element value):
+ *   dfdrho_e = p rho~_e^(p-1) (E0 - Emin) sum_ij dfdCH_ij q_e,ij / |Omega|,
+ *   q_e,ij = (chi_i - u_i)_e^T K0 (chi_j - u_j)_e.
+ * dfdrho: device, N floats. */
+int homo_sensitivity(homo_ctx* ctx, const double dfdCH[36], float* dfdrho);
+
+/* Optimality-criteria update (Sec. 3.3; step limit, damping and minimum density of
+ * Sec. 6): rho_new = clamp(rho (max(-dfdrho,0)/lambda)^damp, max(rho_min, rho-move),
+ * min(1, rho+move)) with the multiplier lambda found on the device so that
+ * mean(rho_new) equals volfrac (the side with mean <= volfrac is returned).
+ *   dfdrho: device N floats (sensitivity w.r.t. rho); rho: device N floats, in/out.
+ *   change_out: host, nullable: max |rho_new - rho|. */
+int homo_update(homo_ctx* ctx, const float* dfdrho, float* rho, double volfrac,
+                double move, double damp, double rho_min, double* change_out);
+
+/* Objective value and gradient (host arithmetic only, Eq. 19-22).
+ *   kind: HOMO_OBJ_*; iteration: loop counter l (HOMO_OBJ_POISSON uses beta^l);
+ *   param: beta for HOMO_OBJ_POISSON, E0 for HOMO_OBJ_LOGPOISSON, ignored otherwise.
+ *   CH: 36 doubles in; f_out: 1 double out; dfdCH: 36 doubles out. */
+int homo_objective(int kind, const double CH[36], int iteration, double param,
+                   double* f_out, double dfdCH[36]);
+
+/* The 24x24 element matrix K0 the library uses (unit modulus, unit voxel, host
+ * arithmetic only): the bilinear form of isotropic elasticity (Sec. 3.2) integrated in
+ * closed form over a trilinear brick. Row/column 3j + comp, local vertex j = a+2b+4c.
+ * Ke: host, 576 doubles, row-major. No GPU needed. */
+int homo_element_matrix(double nu, double Ke[576]);
+
+/* ---- Introspection and operator access (device pointers, 6-case layout above) ---- */
+
+/* Copy the current 6 displacement fields out / in (18*N floats, device). */
+int homo_get_displacement(homo_ctx* ctx, float* u);
+int homo_set_displacement(homo_ctx* ctx, const float* u);
+
+/* Assembled macro-strain loads f_i = sum_e E_e K0 chi_i,e for the current density
+ * (Eq. 4 in the vertex form Eq. 11, element-relative chi of Eq. 12). f: 18*N floats. */
+int homo_get_loads(homo_ctx* ctx, float* f);
+
+/* out = K(E) u on the finest level, matrix-free (Eq. 13), for the 6 cases.
+ * u, out: device, 18*N floats, must not alias. */
+int homo_apply_K(homo_ctx* ctx, const float* u, float* out);
+
+/* Galerkin stencil of level l >= 1 (Eq. 17-18): out[(v*27 + d)*9 + 3r + c], vertex v of
+ * level l in x-fastest order, neighbour offset d = (dx+1) + 3(dy+1) + 9(dz+1), 3x3 block
+ * row r, column c. out: device, 243 * n_l^3 floats. Builds the hierarchy if stale. */
+int homo_get_stencil(homo_ctx* ctx, int level, float* out);
+
+/* Restriction R = I^T from level l to l+1 and prolongation I from l+1 to l (trilinear,
+ * periodic, Sec. 3.3). 6-case layouts on the respective level sizes. restrict: coarse =
+ * R fine; prolong: fine = I coarse (overwrites). */
+int homo_restrict(homo_ctx* ctx, int level, const float* fine, float* coarse);
+int homo_prolong(homo_ctx* ctx, int level, const float* coarse, float* fine);
+
+/* One 8-colour block Gauss-Seidel sweep (Eq. 15-16) on level l, in place on u, colours
+ * 0..7 (reverse = 0) or 7..0 (reverse = 1). f, u: device, 6-case layout on level l. */
+int homo_smooth(homo_ctx* ctx, int level, int reverse, const float* f, float* u);
+
+/* z = M r with M one symmetric V-cycle from a zero initial guess (Alg. 1), the CG
+ * preconditioner. r, z: device, 18*N floats, must not alias. */
+int homo_vcycle(homo_ctx* ctx, const float* r, float* z);
+
+/* ---- Measurement ---- */
+
+/* Kernel classes for per-class device timing. */
+#define HOMO_KC_FINE_MATVEC 0      /* CG product q = K p on the finest level (Eq. 13)      */
+#define HOMO_KC_FINE_RESIDUAL 1    /* finest-level residuals (V-cycle and true residual)   */
+#define HOMO_KC_FINE_GS 2          /* finest-level Gauss-Seidel colour passes (Eq. 15-16)  */
+#define HOMO_KC_COARSE_GS 3        /* coarse-level Gauss-Seidel colour passes              */
+#define HOMO_KC_COARSE_RESIDUAL 4  /* coarse-level residuals                               */
+#define HOMO_KC_TRANSFER 5         /* restriction and prolongation                          */
+#define HOMO_KC_COARSEST 6         /* coarsest direct solve                                 */
+#define HOMO_KC_SETUP 7            /* loads, Galerkin assembly, coarsest factorisation      */
+#define HOMO_KC_CG_VECTOR 8        /* CG vector updates, dot products, scalars              */
+#define HOMO_KC_ELEMENT 9          /* C^H and sensitivity element kernels                   */
+#define HOMO_KC_FILTER 10          /* density filter                                        */
+#define HOMO_KC_OC 11              /* OC update                                             */
+#define HOMO_KC_OTHER 12           /* SIMP moduli, field copies, stencil export             */
+#define HOMO_KC_COUNT 13
+
+/* Start (enable = 1, counters reset) or stop (0) recording a CUDA event pair around
+ * every kernel launch of the context, on its stream. */
+int homo_profile_enable(homo_ctx* ctx, int enable);
+
+/* Synchronise the stream and return, for kernel class kc, the number of kernels
+ * launched and their summed device time in ms since profiling was enabled. */
+int homo_profile_read(homo_ctx* ctx, int kc, long long* launches, double* total_ms);
+
+/* Static name of a kernel class ("fine_matvec", ...), or "" for an unknown class. */
+const char* homo_kernel_class_name(int kc);
+
+/* Total number of kernels this context has launched since it was created. */
+long long homo_launch_count(const homo_ctx* ctx);
+
+/* Residual history of the last homo_solve_cases: one row of 6 relative residuals
+ * ||r_i||/||f_i|| per record (the initial true residual, every CG iteration, and the
+ * true residual that closes every restart cycle). Copies min(rows, capacity) rows to out
+ * (host, 6*capacity doubles) and returns the number of rows (negative on error). */
+int homo_residual_history(const homo_ctx* ctx, double* out, int capacity);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOMO_H */

@@ -38,6 +38,7 @@ from .fem import (  # noqa: F401
     homogenized_tensor,
     sensitivity,
     apply_K_at_vertices,
+    macro_strain_loads_at_vertices,
     homogenize,
 )
 from .filters import cone_filter, cone_weights  # noqa: F401

@@ -219,6 +219,26 @@ def apply_K_at_vertices(n: int, Ee: np.ndarray, Ke: np.ndarray, u: np.ndarray,
     return out
 
 
+def macro_strain_loads_at_vertices(n: int, Ee: np.ndarray, Ke: np.ndarray, chi: np.ndarray,
+                                   vertices: np.ndarray) -> np.ndarray:
+    """f^i_v at the given vertices by the vertex form of Eq. 11:
+    f^i_v = sum over incident elements e of E_e sum_j K0_[7-e, j] chi^i_(e, j).
+    Returns (6, len(vertices), 3)."""
+    v = np.asarray(vertices, dtype=np.int64)
+    x, y, z = v % n, (v // n) % n, v // (n * n)
+    Ee = np.asarray(Ee, dtype=np.float64)
+    fe = Ke @ chi.T                                   # (24, 6)
+    out = np.zeros((6, v.size, 3))
+    for e in range(8):
+        a, b, c = e & 1, (e >> 1) & 1, (e >> 2) & 1
+        ox, oy, oz = (x - 1 + a) % n, (y - 1 + b) % n, (z - 1 + c) % n
+        Eel = Ee[ox + n * (oy + n * oz)]
+        row = 7 - e
+        for i in range(6):
+            out[i] += Eel[:, None] * fe[3 * row:3 * row + 3, i][None, :]
+    return out
+
+
 def homogenize(rho_t: np.ndarray, n: int, E0: float = 1.0, nu: float = 0.3, p: float = 3.0,
                Emin: float = 1e-9, method: str = "lu") -> dict:
     """Solve the 6 cell problems for the physical density rho_t and return C^H and its parts."""

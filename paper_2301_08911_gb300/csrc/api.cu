@@ -1,0 +1,678 @@
+// C ABI of the library (include/homo.h): context life cycle, the multigrid-preconditioned
+// CG driver for the 6 cell problems, C^H, sensitivities, filter and OC update.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "homo_internal.cuh"
+
+using namespace homo;
+
+namespace {
+
+thread_local std::string g_create_err;
+
+int set_err(homo_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_err = msg;
+  return code;
+}
+
+int cuda_err(homo_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return set_err(c, e == cudaErrorMemoryAllocation ? HOMO_ENOMEM : HOMO_ECUDA, m);
+}
+
+#define CK(ctx, call)                                      \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call); \
+  } while (0)
+
+#define RET(x)                      \
+  do {                              \
+    int r_ = (x);                   \
+    if (r_ != HOMO_OK) return r_;   \
+  } while (0)
+
+template <typename T>
+int dalloc(homo_ctx* c, T** p, size_t count, const char* what) {
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_err(c, e, what);
+  }
+  return HOMO_OK;
+}
+
+void free_all(homo_ctx* c) {
+  auto f = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  f(c->rho); f(c->E); f(c->u); f(c->ulo); f(c->f); f(c->r); f(c->z); f(c->pv); f(c->q);
+  f(c->tmp); f(c->A); f(c->G); f(c->part); f(c->scal);
+  for (int l = 0; l < kMaxLevels; ++l) {
+    f(c->lev[l].st); f(c->lev[l].x); f(c->lev[l].b); f(c->lev[l].t);
+  }
+  if (c->hscal) cudaFreeHost(c->hscal);
+  for (auto& r : c->pending) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+}
+
+bool valid_ptr(const void* p) { return p != nullptr; }
+
+cudaEvent_t take_event(homo_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Accumulate the recorded event pairs; the stream must have been synchronised.
+void prof_flush(homo_ctx* c) {
+  for (auto& r : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      c->prof_ms[r.kc] += ms;
+    }
+    c->event_pool.push_back(r.a);
+    c->event_pool.push_back(r.b);
+  }
+  c->pending.clear();
+}
+
+// Counts the kernels of one launcher call and, when profiling, brackets them with events.
+struct Prof {
+  homo_ctx* c;
+  int kc;
+  cudaEvent_t a = nullptr;
+  Prof(homo_ctx* ctx, int k, int nkernels) : c(ctx), kc(k) {
+    c->launches += nkernels;
+    if (c->prof) {
+      c->prof_n[kc] += nkernels;
+      if (c->pending.size() > 8192 && cudaStreamSynchronize(c->stream) == cudaSuccess) prof_flush(c);
+      a = take_event(c);
+      if (a) cudaEventRecord(a, c->stream);
+    }
+  }
+  ~Prof() {
+    if (!a) return;
+    cudaEvent_t b = take_event(c);
+    if (!b) return;
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({kc, a, b});
+  }
+};
+
+#define KL(ctx, kc, nk, call)      \
+  do {                             \
+    Prof prof_(ctx, kc, nk);       \
+    CK(ctx, call);                 \
+  } while (0)
+
+int ensure_loads(homo_ctx* c) {
+  if (!c->density_set) return set_err(c, HOMO_ESTATE, "no density set (call homo_set_density first)");
+  if (!c->loads_valid) {
+    KL(c, HOMO_KC_SETUP, 1, launch_loads(c, c->f));
+    c->loads_valid = true;
+  }
+  return HOMO_OK;
+}
+
+int ensure_hierarchy(homo_ctx* c) {
+  RET(ensure_loads(c));
+  if (c->hier_valid) return HOMO_OK;
+  if (c->nlev == 1) {
+    KL(c, HOMO_KC_SETUP, 1, launch_fine_stencil(c, c->lev[0]));
+  } else {
+    KL(c, HOMO_KC_SETUP, 1, launch_level1_assemble(c, c->lev[1]));
+    for (int l = 1; l + 1 < c->nlev; ++l) KL(c, HOMO_KC_SETUP, 1, launch_galerkin(c->lev[l], c->lev[l + 1], c->stream));
+  }
+  KL(c, HOMO_KC_SETUP, 3, launch_coarsest_setup(c));
+  c->hier_valid = true;
+  return HOMO_OK;
+}
+
+int smooth_level(homo_ctx* c, int l, bool reverse, const float* f, float* x) {
+  for (int k = 0; k < 8; ++k) {
+    const int col = reverse ? 7 - k : k;
+    if (l == 0) KL(c, HOMO_KC_FINE_GS, 1, launch_fine_gs(c, col, f, x));
+    else KL(c, HOMO_KC_COARSE_GS, 1, launch_coarse_gs(c->lev[l], col, f, x, c->stream));
+  }
+  return HOMO_OK;
+}
+
+// z = M r: one symmetric V-cycle (Alg. 1) from a zero initial guess; the post-smoother
+// visits the colours in reverse order so M is symmetric.
+int vcycle(homo_ctx* c, const float* r, float* z) {
+  cudaStream_t s = c->stream;
+  if (c->nlev == 1) {
+    KL(c, HOMO_KC_COARSEST, 1, launch_coarsest_apply(c, r, z));
+    return HOMO_OK;
+  }
+  const int pre = c->opts.pre_sweeps, post = c->opts.post_sweeps;
+  CK(c, cudaMemsetAsync(z, 0, sizeof(float) * kPlanes * c->N, s));
+  for (int k = 0; k < pre; ++k) RET(smooth_level(c, 0, false, r, z));
+  KL(c, HOMO_KC_FINE_RESIDUAL, 1, launch_fine_residual(c, r, z, nullptr, c->q, nullptr, nullptr));
+  KL(c, HOMO_KC_TRANSFER, 1, launch_restrict(c->n, c->q, c->lev[1].b, s));
+  const int L = c->nlev - 1;
+  for (int l = 1; l < L; ++l) {
+    Level& lv = c->lev[l];
+    CK(c, cudaMemsetAsync(lv.x, 0, sizeof(float) * kPlanes * lv.N, s));
+    for (int k = 0; k < pre; ++k) RET(smooth_level(c, l, false, lv.b, lv.x));
+    KL(c, HOMO_KC_COARSE_RESIDUAL, 1, launch_coarse_residual(lv, lv.b, lv.x, lv.t, s));
+    KL(c, HOMO_KC_TRANSFER, 1, launch_restrict(lv.n, lv.t, c->lev[l + 1].b, s));
+  }
+  KL(c, HOMO_KC_COARSEST, 1, launch_coarsest_apply(c, c->lev[L].b, c->lev[L].x));
+  for (int l = L - 1; l >= 1; --l) {
+    Level& lv = c->lev[l];
+    KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(lv.n, c->lev[l + 1].x, lv.x, 0, s));
+    for (int k = 0; k < post; ++k) RET(smooth_level(c, l, true, lv.b, lv.x));
+  }
+  KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(c->n, c->lev[1].x, z, 0, s));
+  for (int k = 0; k < post; ++k) RET(smooth_level(c, 0, true, r, z));
+  return HOMO_OK;
+}
+
+int sync_read(homo_ctx* c, int slot, int count) {
+  CK(c, cudaMemcpyAsync(c->hscal + slot, c->scal + slot, sizeof(double) * count,
+                        cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  return HOMO_OK;
+}
+
+// r = f - K (u + ulo) in double-float arithmetic, with its plane means (the rigid
+// translations, outside the range of K) removed; ||r_c||^2 into S_RR, active flags, read
+// back.
+int true_residual(homo_ctx* c, double tol) {
+  int g = 0;
+  KL(c, HOMO_KC_FINE_RESIDUAL, 1, launch_fine_residual(c, c->f, c->u, c->ulo, c->r, c->part, &g));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RR, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_center(c->r, c->scal, c->N, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_active(c->scal, tol, 1, c->N, c->stream));
+  return sync_read(c, S_RR, 6);
+}
+
+void record_history(homo_ctx* c) {
+  for (int k = 0; k < kCases; ++k) {
+    const double ff = c->hscal[S_FF + k], rr = c->hscal[S_RR + k];
+    c->history.push_back(ff > 0.0 ? std::sqrt(rr / ff) : 0.0);
+  }
+}
+
+int precondition_and_direction(homo_ctx* c, int first) {
+  int g = 0;
+  RET(vcycle(c, c->r, c->z));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_dot6_zsum(c->r, c->z, c->N, c->part, &g, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RZ, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_beta(c->scal, first, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_update_p(c->pv, c->z, c->scal, c->N, c->stream));
+  return HOMO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int homo_version(void) { return 100; }
+
+const char* homo_status_string(int status) {
+  switch (status) {
+    case HOMO_OK: return "ok";
+    case HOMO_EINVAL: return "invalid argument";
+    case HOMO_ENOMEM: return "out of memory";
+    case HOMO_ECUDA: return "CUDA error";
+    case HOMO_ENOCONV: return "not converged within the iteration limit";
+    case HOMO_EDIVERGED: return "diverged (non-finite residual)";
+    case HOMO_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* homo_last_error(const homo_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+int homo_element_matrix(double nu, double Ke[576]) {
+  if (!Ke || !(nu > -1.0 && nu < 0.5)) return HOMO_EINVAL;
+  KeParam ke;
+  LoadParam ld;
+  ChiParam chi;
+  build_element_matrix(nu, ke, ld, chi);
+  for (int i = 0; i < 576; ++i) Ke[i] = ke.k[i];
+  return HOMO_OK;
+}
+
+int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Emin,
+                const homo_opts* opts) {
+  g_create_err.clear();
+  if (!out) return set_err(nullptr, HOMO_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (n < 4 || n > 1024) return set_err(nullptr, HOMO_EINVAL, "n must be in [4, 1024]");
+  if (!(E0 > 0) || !(nu > -1.0 && nu < 0.5) || !(p >= 1.0) || !(Emin >= 0.0 && Emin < E0))
+    return set_err(nullptr, HOMO_EINVAL, "material parameters out of range");
+  homo_opts o{};
+  o.min_coarse = 4;
+  o.max_levels = 0;
+  o.pre_sweeps = 1;
+  o.post_sweeps = 1;
+  if (opts) {
+    if (opts->struct_size != static_cast<int>(sizeof(homo_opts)))
+      return set_err(nullptr, HOMO_EINVAL, "homo_opts.struct_size mismatch");
+    if (opts->min_coarse) o.min_coarse = opts->min_coarse;
+    if (opts->max_levels) o.max_levels = opts->max_levels;
+    if (opts->pre_sweeps) o.pre_sweeps = opts->pre_sweeps;
+    if (opts->post_sweeps) o.post_sweeps = opts->post_sweeps;
+  }
+  if (o.min_coarse < 3 || o.max_levels < 0 || o.max_levels > kMaxLevels || o.pre_sweeps < 0 ||
+      o.post_sweeps < 0 || o.pre_sweeps > 16 || o.post_sweeps > 16 || o.pre_sweeps != o.post_sweeps)
+    return set_err(nullptr, HOMO_EINVAL, "bad homo_opts (min_coarse >= 3, pre == post sweeps <= 16)");
+  int sizes[kMaxLevels];
+  int nlev = 1;
+  sizes[0] = n;
+  while (sizes[nlev - 1] % 2 == 0 && sizes[nlev - 1] / 2 >= o.min_coarse && nlev < kMaxLevels &&
+         (o.max_levels == 0 || nlev < o.max_levels)) {
+    sizes[nlev] = sizes[nlev - 1] / 2;
+    ++nlev;
+  }
+  const int nc = sizes[nlev - 1];
+  if (nc > 8)
+    return set_err(nullptr, HOMO_EINVAL,
+                   "coarsest level has " + std::to_string(nc) +
+                       " cells per axis; at most 8 are solved directly (n = m * 2^k with m <= 8)");
+
+  homo_ctx* c = new (std::nothrow) homo_ctx;
+  if (!c) return set_err(nullptr, HOMO_ENOMEM, "host allocation failed");
+  c->n = n;
+  c->N = static_cast<size_t>(n) * n * n;
+  c->E0 = E0; c->nu = nu; c->p = p; c->Emin = Emin;
+  c->opts = o;
+  c->opts.struct_size = sizeof(homo_opts);
+  build_element_matrix(nu, c->ke, c->ld, c->chi);
+  c->hBf.assign(8 * 576, 0.f);
+  build_level1_tables(c->ke, c->hBf.data());
+  c->nlev = nlev;
+  c->nc = nc;
+  c->mc = 3 * nc * nc * nc;
+
+  int rc = HOMO_OK;
+  const size_t N = c->N, V = kPlanes * N;
+  auto A = [&](float** ptr, size_t cnt, const char* w) {
+    if (rc == HOMO_OK) rc = dalloc(c, ptr, cnt, w);
+  };
+  A(&c->rho, N, "rho"); A(&c->E, N, "E"); A(&c->tmp, N, "tmp");
+  A(&c->u, V, "u"); A(&c->ulo, V, "ulo"); A(&c->f, V, "f"); A(&c->r, V, "r");
+  A(&c->z, V, "z"); A(&c->pv, V, "p"); A(&c->q, V, "q");
+  for (int l = 0; l < nlev; ++l) {
+    Level& L = c->lev[l];
+    L.n = sizes[l];
+    L.N = static_cast<size_t>(L.n) * L.n * L.n;
+    L.colour_blocked = (L.n % 2 == 0);
+    if (l >= 1 || nlev == 1) A(&L.st, kStencil * L.N, "stencil");
+    if (l >= 1) {
+      A(&L.x, kPlanes * L.N, "level x");
+      A(&L.b, kPlanes * L.N, "level b");
+      if (l + 1 < nlev) A(&L.t, kPlanes * L.N, "level t");
+    }
+  }
+  if (rc == HOMO_OK) rc = dalloc(c, &c->A, static_cast<size_t>(c->mc) * c->mc, "coarsest A");
+  if (rc == HOMO_OK) rc = dalloc(c, &c->G, static_cast<size_t>(c->mc) * c->mc, "coarsest G");
+  c->part_cap = static_cast<size_t>(16 * 152) * 32;
+  if (rc == HOMO_OK) rc = dalloc(c, &c->part, c->part_cap, "partials");
+  if (rc == HOMO_OK) rc = dalloc(c, &c->scal, static_cast<size_t>(S_COUNT), "scalars");
+  if (rc == HOMO_OK) {
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&c->hscal), sizeof(double) * S_COUNT);
+    if (e != cudaSuccess) rc = cuda_err(c, e, "pinned scalars");
+  }
+  if (rc == HOMO_OK) {
+    cudaError_t e = cudaMemset(c->u, 0, sizeof(float) * V);
+    if (e == cudaSuccess) e = cudaMemset(c->ulo, 0, sizeof(float) * V);
+    if (e == cudaSuccess) e = cudaMemset(c->scal, 0, sizeof(double) * S_COUNT);
+    if (e != cudaSuccess) rc = cuda_err(c, e, "initial memset");
+  }
+  if (rc != HOMO_OK) {
+    g_create_err = c->err;
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return HOMO_OK;
+}
+
+int homo_destroy(homo_ctx* ctx) {
+  if (!ctx) return HOMO_OK;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  free_all(ctx);
+  delete ctx;
+  return HOMO_OK;
+}
+
+int homo_set_stream(homo_ctx* ctx, void* cuda_stream) {
+  if (!ctx) return HOMO_EINVAL;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  return HOMO_OK;
+}
+
+int homo_num_levels(const homo_ctx* ctx) { return ctx ? ctx->nlev : -HOMO_EINVAL; }
+
+int homo_level_size(const homo_ctx* ctx, int level) {
+  if (!ctx || level < 0 || level >= ctx->nlev) return -HOMO_EINVAL;
+  return ctx->lev[level].n;
+}
+
+int homo_filter(homo_ctx* ctx, double radius, const float* in, float* out) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!valid_ptr(in) || !valid_ptr(out) || in == out)
+    return set_err(ctx, HOMO_EINVAL, "filter: null or aliased buffers");
+  FilterParam fp;
+  if (build_filter_param(radius, fp) != HOMO_OK)
+    return set_err(ctx, HOMO_EINVAL, "filter radius must be in (0, 3.5]");
+  KL(ctx, HOMO_KC_FILTER, 1, launch_filter(fp, ctx->n, in, out, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_set_density(homo_ctx* ctx, const float* rho, int on_device) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!valid_ptr(rho)) return set_err(ctx, HOMO_EINVAL, "set_density: null rho");
+  const float* src = rho;
+  if (!on_device) {
+    CK(ctx, cudaMemcpyAsync(ctx->rho, rho, sizeof(float) * ctx->N, cudaMemcpyHostToDevice, ctx->stream));
+    src = ctx->rho;
+  }
+  KL(ctx, HOMO_KC_OTHER, 1, launch_simp(src, ctx->rho, ctx->E, ctx->N, static_cast<float>(ctx->p),
+                      static_cast<float>(ctx->E0), static_cast<float>(ctx->Emin), ctx->stream));
+  ctx->density_set = true;
+  ctx->loads_valid = false;
+  ctx->hier_valid = false;
+  ctx->solved = false;
+  return HOMO_OK;
+}
+
+int homo_solve_cases(homo_ctx* ctx, double rel_tol, int max_iters, int warm_start,
+                     int iters_out[6], double relres_out[6]) {
+  if (!ctx) return HOMO_EINVAL;
+  homo_ctx* c = ctx;
+  if (!(rel_tol > 0.0) || max_iters < 1) return set_err(c, HOMO_EINVAL, "rel_tol > 0 and max_iters >= 1 required");
+  RET(ensure_hierarchy(c));
+  const size_t V = kPlanes * c->N;
+  if (!warm_start) {
+    CK(c, cudaMemsetAsync(c->u, 0, sizeof(float) * V, c->stream));
+    CK(c, cudaMemsetAsync(c->ulo, 0, sizeof(float) * V, c->stream));
+  }
+  int g = 0;
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_dot6(c->f, c->f, c->N, c->part, &g, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases, c->scal + S_FF, c->stream));
+  // the coarsest factorisation reports a failed pivot in an int next to the OC slots
+  int its[kCases] = {0, 0, 0, 0, 0, 0};
+  int total = 0;
+  bool diverged = false;
+  RET(true_residual(c, rel_tol));
+  RET(sync_read(c, S_FF, 6));
+  RET(sync_read(c, S_OC + 63, 1));
+  int piv_fail = 0;
+  std::memcpy(&piv_fail, c->hscal + S_OC + 63, sizeof(int));
+  if (piv_fail) return set_err(c, HOMO_EDIVERGED, "coarsest operator is not positive definite");
+  auto any_active = [&](double* rr) {
+    bool a = false;
+    for (int k = 0; k < kCases; ++k) {
+      if (!std::isfinite(rr[k])) diverged = true;
+      if (c->hscal[S_FF + k] > 0.0 && rr[k] > rel_tol * rel_tol * c->hscal[S_FF + k]) a = true;
+    }
+    return a;
+  };
+  c->history.clear();
+  record_history(c);
+  // Restarted CG (mixed-precision iterative refinement, u kept in double-float): a cycle
+  // runs on the FP32 recursive residual, whose plane means are removed after every
+  // update (K cannot produce a rigid translation, and the V-cycle would amplify one). A
+  // cycle ends when every case meets rel_tol, has reduced its residual by kCycleDrop, or
+  // starts to grow; the next cycle starts from the accurate true residual.
+  constexpr double kCycleDrop = 1e-5;
+  double rr0[kCases], rrmin[kCases];
+  for (int restart = 0; restart < 24 && !diverged; ++restart) {
+    if (!any_active(c->hscal + S_RR) || total >= max_iters) break;
+    for (int k = 0; k < kCases; ++k) rr0[k] = rrmin[k] = c->hscal[S_RR + k];
+    RET(precondition_and_direction(c, 1));
+    while (total < max_iters) {
+      ++total;
+      for (int k = 0; k < kCases; ++k)
+        if (c->hscal[S_FF + k] > 0.0 && c->hscal[S_RR + k] > rel_tol * rel_tol * c->hscal[S_FF + k]) ++its[k];
+      KL(c, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(c, c->pv, c->q, 1, c->part, &g));
+      KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_PQ, c->stream));
+      KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_alpha(c->scal, c->stream));
+      KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_update_xr(c->u, c->ulo, c->r, c->pv, c->q, c->scal, c->N, c->part, &g, c->stream));
+      KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RR, c->stream));
+      KL(c, HOMO_KC_CG_VECTOR, 1, launch_center(c->r, c->scal, c->N, c->stream));
+      KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_active(c->scal, rel_tol, 1, c->N, c->stream));
+      RET(sync_read(c, S_RR, 6));
+      record_history(c);
+      if (!any_active(c->hscal + S_RR) || diverged) break;
+      bool cycle_done = true, blowup = false;
+      for (int k = 0; k < kCases; ++k) {
+        const double rr = c->hscal[S_RR + k], ff = c->hscal[S_FF + k];
+        const bool act = ff > 0.0 && rr > rel_tol * rel_tol * ff;
+        if (act && rr > kCycleDrop * kCycleDrop * rr0[k]) cycle_done = false;
+        if (rr > 1e4 * rrmin[k]) blowup = true;
+        rrmin[k] = std::min(rrmin[k], rr);
+      }
+      if (cycle_done || blowup) break;
+      RET(precondition_and_direction(c, 0));
+    }
+    if (diverged) break;
+    RET(true_residual(c, rel_tol));   // recursive and true residual can drift apart
+    record_history(c);
+  }
+  c->solved = true;
+  bool conv = true;
+  for (int k = 0; k < kCases; ++k) {
+    const double ff = c->hscal[S_FF + k], rr = c->hscal[S_RR + k];
+    const double rel = ff > 0.0 ? std::sqrt(rr / ff) : 0.0;
+    if (!std::isfinite(rr)) diverged = true;
+    if (ff > 0.0 && !(rel <= rel_tol)) conv = false;
+    if (relres_out) relres_out[k] = rel;
+    if (iters_out) iters_out[k] = its[k];
+  }
+  if (diverged) return set_err(c, HOMO_EDIVERGED, "non-finite residual in CG");
+  if (!conv) return set_err(c, HOMO_ENOCONV, "relative residual above tolerance after max_iters");
+  return HOMO_OK;
+}
+
+int homo_CH(homo_ctx* ctx, double CH[36]) {
+  if (!ctx || !CH) return HOMO_EINVAL;
+  if (!ctx->solved) return set_err(ctx, HOMO_ESTATE, "homo_CH needs a solve first");
+  int g = 0;
+  KL(ctx, HOMO_KC_ELEMENT, 1, launch_fine_elem(ctx, 0, nullptr, nullptr, ctx->part, &g));
+  KL(ctx, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(ctx->part, g, 21, ctx->scal + S_CH, ctx->stream));
+  RET(sync_read(ctx, S_CH, 21));
+  int idx = 0;
+  const double invN = 1.0 / static_cast<double>(ctx->N);
+  for (int i = 0; i < kCases; ++i)
+    for (int j = i; j < kCases; ++j) {
+      const double v = ctx->hscal[S_CH + idx++] * invN;
+      CH[6 * i + j] = v;
+      CH[6 * j + i] = v;
+    }
+  return HOMO_OK;
+}
+
+int homo_sensitivity(homo_ctx* ctx, const double dfdCH[36], float* dfdrho) {
+  if (!ctx || !dfdCH || !dfdrho) return HOMO_EINVAL;
+  if (!ctx->solved) return set_err(ctx, HOMO_ESTATE, "homo_sensitivity needs a solve first");
+  KL(ctx, HOMO_KC_ELEMENT, 1, launch_fine_elem(ctx, 1, dfdCH, dfdrho, nullptr, nullptr));
+  return HOMO_OK;
+}
+
+int homo_update(homo_ctx* ctx, const float* dfdrho, float* rho, double volfrac, double move,
+                double damp, double rho_min, double* change_out) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!dfdrho || !rho || static_cast<const void*>(dfdrho) == static_cast<const void*>(rho))
+    return set_err(ctx, HOMO_EINVAL, "update: null or aliased buffers");
+  if (!(volfrac > 0.0 && volfrac <= 1.0) || !(move > 0.0) || !(damp > 0.0) ||
+      !(rho_min >= 0.0 && rho_min < 1.0))
+    return set_err(ctx, HOMO_EINVAL, "update: parameters out of range");
+  KL(ctx, HOMO_KC_OC, kOcKernels, launch_oc(ctx, dfdrho, rho, volfrac, move, damp, rho_min, change_out));
+  return HOMO_OK;
+}
+
+int homo_objective(int kind, const double CH[36], int iteration, double param, double* f_out,
+                   double dfdCH[36]) {
+  if (!CH || !f_out || !dfdCH) return HOMO_EINVAL;
+  auto C = [&](int i, int j) { return CH[6 * i + j]; };
+  for (int i = 0; i < 36; ++i) dfdCH[i] = 0.0;
+  switch (kind) {
+    case HOMO_OBJ_BULK:
+      *f_out = -(C(0, 0) + C(1, 1) + C(2, 2) + 2.0 * (C(0, 1) + C(0, 2) + C(1, 2))) / 9.0;
+      for (int i = 0; i < 3; ++i) dfdCH[7 * i] = -1.0 / 9.0;
+      dfdCH[1] = dfdCH[2] = dfdCH[8] = -2.0 / 9.0;
+      return HOMO_OK;
+    case HOMO_OBJ_SHEAR:
+      *f_out = -(C(3, 3) + C(4, 4) + C(5, 5)) / 3.0;
+      for (int i = 3; i < 6; ++i) dfdCH[7 * i] = -1.0 / 3.0;
+      return HOMO_OK;
+    case HOMO_OBJ_POISSON: {
+      const double bl = std::pow(param, iteration);
+      *f_out = C(0, 1) + C(0, 2) + C(1, 2) - bl * (C(0, 0) + C(1, 1) + C(2, 2));
+      dfdCH[1] = dfdCH[2] = dfdCH[8] = 1.0;
+      for (int i = 0; i < 3; ++i) dfdCH[7 * i] = -bl;
+      return HOMO_OK;
+    }
+    case HOMO_OBJ_LOGPOISSON: {
+      const double eta = 0.6, gamma = 0.5;
+      const double E0 = param > 0 ? param : 1.0;
+      const double tau = -1.0 / std::pow(E0, gamma);
+      const double a = C(0, 1) + C(1, 2) + C(2, 0), b = C(0, 0) + C(1, 1) + C(2, 2);
+      if (!(b > 0)) return HOMO_EINVAL;
+      const double t = 1.0 + eta * a / b;
+      *f_out = std::log(t) + tau * std::pow(b, gamma);
+      const double da = eta / b / t;
+      const double db = -eta * a / (b * b) / t + tau * gamma * std::pow(b, gamma - 1.0);
+      dfdCH[1] = dfdCH[8] = dfdCH[12] = da;   // (0,1), (1,2), (2,0)
+      for (int i = 0; i < 3; ++i) dfdCH[7 * i] = db;
+      return HOMO_OK;
+    }
+    default:
+      return HOMO_EINVAL;
+  }
+}
+
+int homo_get_displacement(homo_ctx* ctx, float* u) {
+  if (!ctx || !u) return HOMO_EINVAL;
+  KL(ctx, HOMO_KC_OTHER, 1, launch_split_get(ctx->u, ctx->ulo, u, kPlanes * ctx->N, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_set_displacement(homo_ctx* ctx, const float* u) {
+  if (!ctx || !u) return HOMO_EINVAL;
+  KL(ctx, HOMO_KC_OTHER, 1, launch_split_set(ctx->u, ctx->ulo, u, kPlanes * ctx->N, ctx->stream));
+  ctx->solved = false;
+  return HOMO_OK;
+}
+
+int homo_get_loads(homo_ctx* ctx, float* f) {
+  if (!ctx || !f) return HOMO_EINVAL;
+  RET(ensure_loads(ctx));
+  CK(ctx, cudaMemcpyAsync(f, ctx->f, sizeof(float) * kPlanes * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_apply_K(homo_ctx* ctx, const float* u, float* out) {
+  if (!ctx || !u || !out || u == out) return HOMO_EINVAL;
+  if (!ctx->density_set) return set_err(ctx, HOMO_ESTATE, "no density set");
+  KL(ctx, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(ctx, u, out, 1, nullptr, nullptr));
+  return HOMO_OK;
+}
+
+int homo_get_stencil(homo_ctx* ctx, int level, float* out) {
+  if (!ctx || !out || level < 0 || level >= ctx->nlev) return HOMO_EINVAL;
+  RET(ensure_hierarchy(ctx));
+  if (level == 0 && !ctx->lev[0].st) {
+    Level tmp = ctx->lev[0];
+    if (dalloc(ctx, &tmp.st, kStencil * tmp.N, "temporary level-0 stencil") != HOMO_OK) return HOMO_ENOMEM;
+    cudaError_t e = launch_fine_stencil(ctx, tmp);
+    if (e == cudaSuccess) e = launch_stencil_export(tmp, out, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp.st);
+    if (e != cudaSuccess) return cuda_err(ctx, e, "level-0 stencil export");
+    return HOMO_OK;
+  }
+  KL(ctx, HOMO_KC_OTHER, 1, launch_stencil_export(ctx->lev[level], out, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_restrict(homo_ctx* ctx, int level, const float* fine, float* coarse) {
+  if (!ctx || !fine || !coarse || level < 0 || level + 1 >= ctx->nlev) return HOMO_EINVAL;
+  KL(ctx, HOMO_KC_TRANSFER, 1, launch_restrict(ctx->lev[level].n, fine, coarse, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_prolong(homo_ctx* ctx, int level, const float* coarse, float* fine) {
+  if (!ctx || !fine || !coarse || level < 0 || level + 1 >= ctx->nlev) return HOMO_EINVAL;
+  KL(ctx, HOMO_KC_TRANSFER, 1, launch_prolong_add(ctx->lev[level].n, coarse, fine, 1, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_smooth(homo_ctx* ctx, int level, int reverse, const float* f, float* u) {
+  if (!ctx || !f || !u || level < 0 || level >= ctx->nlev) return HOMO_EINVAL;
+  if (ctx->lev[level].n % 2 != 0) return set_err(ctx, HOMO_EINVAL, "smoothing needs an even level size");
+  RET(ensure_hierarchy(ctx));
+  return smooth_level(ctx, level, reverse != 0, f, u);
+}
+
+int homo_vcycle(homo_ctx* ctx, const float* r, float* z) {
+  if (!ctx || !r || !z || r == z) return HOMO_EINVAL;
+  RET(ensure_hierarchy(ctx));
+  return vcycle(ctx, r, z);
+}
+
+int homo_profile_enable(homo_ctx* ctx, int enable) {
+  if (!ctx) return HOMO_EINVAL;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  for (int k = 0; k < HOMO_KC_COUNT; ++k) {
+    ctx->prof_n[k] = 0;
+    ctx->prof_ms[k] = 0.0;
+  }
+  ctx->prof = enable != 0;
+  return HOMO_OK;
+}
+
+int homo_profile_read(homo_ctx* ctx, int kc, long long* launches, double* total_ms) {
+  if (!ctx || kc < 0 || kc >= HOMO_KC_COUNT) return HOMO_EINVAL;
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  prof_flush(ctx);
+  if (launches) *launches = ctx->prof_n[kc];
+  if (total_ms) *total_ms = ctx->prof_ms[kc];
+  return HOMO_OK;
+}
+
+const char* homo_kernel_class_name(int kc) {
+  static const char* names[HOMO_KC_COUNT] = {
+      "fine_matvec", "fine_residual", "fine_gs", "coarse_gs", "coarse_residual", "transfer", "coarsest",
+      "setup", "cg_vector", "element", "filter", "oc", "other"};
+  return (kc >= 0 && kc < HOMO_KC_COUNT) ? names[kc] : "";
+}
+
+long long homo_launch_count(const homo_ctx* ctx) { return ctx ? ctx->launches : -1; }
+
+int homo_residual_history(const homo_ctx* ctx, double* out, int capacity) {
+  if (!ctx || capacity < 0 || (capacity > 0 && !out)) return -HOMO_EINVAL;
+  const int rows = static_cast<int>(ctx->history.size() / kCases);
+  const int m = std::min(rows, capacity);
+  for (int i = 0; i < m * kCases; ++i) out[i] = ctx->history[i];
+  return rows;
+}
+
+}  // extern "C"

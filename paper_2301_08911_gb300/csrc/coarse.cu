@@ -1,0 +1,480 @@
+// Coarse levels of the multigrid hierarchy (Sec. 3.3, Sec. 4.2): Galerkin stencils,
+// stored-stencil relaxation and residual, trilinear transfers and the direct coarsest
+// solve with the rigid-translation null space projected out.
+#include "dev_common.cuh"
+
+namespace homo {
+
+namespace {
+
+struct BfParam {
+  float b[8 * 576];   // B_f = P_f^T K0 P_f for the 8 fine elements of a coarse element
+};
+
+// Level-1 stencil from the fine moduli (Eq. 17-18, grouped per coarse element): the
+// coarse element with origin O has matrix sum_f E[2O + f] B_f; vertex V is local vertex
+// 7 - t of its incident coarse element t, and local vertex J of that element is the
+// neighbour V + bits(t) + bits(J) - 1. One thread per coarse vertex.
+__global__ void __launch_bounds__(128) k_level1(const __grid_constant__ BfParam B,
+                                                const float* __restrict__ E, int nf,
+                                                float* __restrict__ st, int nc, bool cb) {
+  const size_t Nc = static_cast<size_t>(nc) * nc * nc;
+  for (size_t p = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < Nc;
+       p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int X, Y, Z;
+    vertex_of_pos(p, nc, cb, X, Y, Z);
+    // fine elements of the 4x4x4 box with origin 2V - (2,2,2)
+    float Eb[64];
+    int ix[4], iy[4], iz[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ix[a] = ((2 * X - 2 + a) % nf + nf) % nf;
+      iy[a] = (((2 * Y - 2 + a) % nf + nf) % nf) * nf;
+      iz[a] = (((2 * Z - 2 + a) % nf + nf) % nf) * nf * nf;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) Eb[a + 4 * b + 16 * c] = __ldg(E + ix[a] + iy[b] + iz[c]);
+#pragma unroll 1
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      float A[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) A[q] = 0.f;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int ta = t & 1, tb = (t >> 1) & 1, tc = t >> 2;
+        const int Ja = dx + 1 - ta, Jb = dy + 1 - tb, Jc = dz + 1 - tc;
+        if (Ja < 0 || Ja > 1 || Jb < 0 || Jb > 1 || Jc < 0 || Jc > 1) continue;
+        const int J = Ja + 2 * Jb + 4 * Jc, row = 7 - t;
+#pragma unroll
+        for (int f = 0; f < 8; ++f) {
+          const float Ef = Eb[(2 * ta + (f & 1)) + 4 * (2 * tb + ((f >> 1) & 1)) + 16 * (2 * tc + (f >> 2))];
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              A[3 * r + c] = fmaf(Ef, B.b[f * 576 + (3 * row + r) * 24 + 3 * J + c], A[3 * r + c]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) st[static_cast<size_t>(9 * d + q) * Nc + p] = A[q];
+    }
+  }
+}
+
+// Galerkin product R K I on vertex stencils (Sec. 3.3): the block between coarse vertex V
+// and V + d is sum over fine a near 2V and b near 2(V+d), |b - a| <= 1, of
+// w(a - 2V) w(b - 2V - 2d) K_(a, b - a), with tent weights w(e) = prod (1 - |e_k|/2).
+// One thread per (coarse vertex, d); consecutive threads take consecutive stencil
+// positions so the stores are coalesced.
+__global__ void __launch_bounds__(256) k_galerkin(const float* __restrict__ sf, int nf, bool cbf,
+                                                  float* __restrict__ sc, int nc, bool cbc) {
+  const size_t Nf = static_cast<size_t>(nf) * nf * nf;
+  const size_t Nc = static_cast<size_t>(nc) * nc * nc;
+  const size_t total = 27 * Nc;
+  for (size_t it = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; it < total;
+       it += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int d = static_cast<int>(it / Nc);
+    const size_t p = it - static_cast<size_t>(d) * Nc;
+    int X, Y, Z;
+    vertex_of_pos(p, nc, cbc, X, Y, Z);
+    const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    float A[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A[q] = 0.f;
+    for (int az = -1; az <= 1; ++az)
+      for (int ay = -1; ay <= 1; ++ay)
+        for (int ax = -1; ax <= 1; ++ax) {
+          const float wa = (1.f - 0.5f * abs(ax)) * (1.f - 0.5f * abs(ay)) * (1.f - 0.5f * abs(az));
+          const int fx = ((2 * X + ax) % nf + nf) % nf, fy = ((2 * Y + ay) % nf + nf) % nf,
+                    fz = ((2 * Z + az) % nf + nf) % nf;
+          const size_t pa = stencil_pos(fx, fy, fz, nf, cbf);
+          const int a3[3] = {ax, ay, az};
+          // b - 2V = 2D + e, e in {-1,0,1}; need |b - a| <= 1
+          for (int ez = -1; ez <= 1; ++ez) {
+            const int bz = 2 * D[2] + ez - a3[2];
+            if (bz < -1 || bz > 1) continue;
+            for (int ey = -1; ey <= 1; ++ey) {
+              const int by = 2 * D[1] + ey - a3[1];
+              if (by < -1 || by > 1) continue;
+              for (int ex = -1; ex <= 1; ++ex) {
+                const int bx = 2 * D[0] + ex - a3[0];
+                if (bx < -1 || bx > 1) continue;
+                const float wb = (1.f - 0.5f * abs(ex)) * (1.f - 0.5f * abs(ey)) * (1.f - 0.5f * abs(ez));
+                const float ww = wa * wb;
+                const int dd = (bx + 1) + 3 * (by + 1) + 9 * (bz + 1);
+#pragma unroll
+                for (int q = 0; q < 9; ++q)
+                  A[q] = fmaf(ww, __ldg(sf + static_cast<size_t>(9 * dd + q) * Nf + pa), A[q]);
+              }
+            }
+          }
+        }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) sc[static_cast<size_t>(9 * d + q) * Nc + p] = A[q];
+  }
+}
+
+__device__ __forceinline__ void solve3x6c(const float (&S)[9], float (&b)[18]) {
+  const float d0 = S[0];
+  const float l10 = S[3] / d0, l20 = S[6] / d0;
+  const float d1 = S[4] - l10 * S[1];
+  const float l21 = (S[7] - l20 * S[1]) / d1;
+  const float d2 = S[8] - l20 * S[2] - l21 * (S[5] - l10 * S[2]);
+  const float i0 = 1.f / d0, i1 = 1.f / d1, i2 = 1.f / d2;
+#pragma unroll
+  for (int c = 0; c < kCases; ++c) {
+    float y0 = b[3 * c], y1 = b[3 * c + 1], y2 = b[3 * c + 2];
+    y1 -= l10 * y0;
+    y2 -= l20 * y0 + l21 * y1;
+    const float x2 = y2 * i2;
+    const float x1 = y1 * i1 - l21 * x2;
+    const float x0 = y0 * i0 - l10 * x1 - l20 * x2;
+    b[3 * c] = x0;
+    b[3 * c + 1] = x1;
+    b[3 * c + 2] = x2;
+  }
+}
+
+// One colour pass of block Gauss-Seidel (Eq. 15-16) with the stored stencil.
+__global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
+                                                   const float* __restrict__ f,
+                                                   float* __restrict__ x, int n, int colour) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  const int h = n >> 1;
+  const size_t Nh = static_cast<size_t>(h) * h * h;
+  const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
+  for (size_t m = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < Nh;
+       m += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int X = 2 * static_cast<int>(m % h) + cx;
+    const int Y = 2 * static_cast<int>((m / h) % h) + cy;
+    const int Z = 2 * static_cast<int>(m / (static_cast<size_t>(h) * h)) + cz;
+    const size_t p = static_cast<size_t>(colour) * Nh + m;
+    const size_t v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
+    const Nb nb = make_nb(X, Y, Z, n);
+    float rhs[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) rhs[q] = __ldg(f + q * N + v);
+    float S[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) S[q] = __ldg(st + static_cast<size_t>(9 * 13 + q) * N + p);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      if (d == 13) continue;
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      float A[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) A[q] = __ldg(st + static_cast<size_t>(9 * d + q) * N + p);
+      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+#pragma unroll
+      for (int c = 0; c < kCases; ++c) {
+        const float u0 = x[(3 * c) * N + w], u1 = x[(3 * c + 1) * N + w], u2 = x[(3 * c + 2) * N + w];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          rhs[3 * c + r] -= fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, A[3 * r + 2] * u2));
+      }
+    }
+    solve3x6c(S, rhs);
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) x[q * N + v] = rhs[q];
+  }
+}
+
+// out = b - K x with the stored stencil; threads walk stencil positions (coalesced).
+__global__ void __launch_bounds__(256) k_coarse_residual(const float* __restrict__ st,
+                                                         const float* __restrict__ b,
+                                                         const float* __restrict__ x,
+                                                         float* __restrict__ out, int n, bool cb) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t p = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < N;
+       p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int X, Y, Z;
+    vertex_of_pos(p, n, cb, X, Y, Z);
+    const size_t v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
+    const Nb nb = make_nb(X, Y, Z, n);
+    float acc[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      float A[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) A[q] = __ldg(st + static_cast<size_t>(9 * d + q) * N + p);
+      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+#pragma unroll
+      for (int c = 0; c < kCases; ++c) {
+        const float u0 = __ldg(x + (3 * c) * N + w), u1 = __ldg(x + (3 * c + 1) * N + w),
+                    u2 = __ldg(x + (3 * c + 2) * N + w);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          acc[3 * c + r] = fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, fmaf(A[3 * r + 2], u2, acc[3 * c + r])));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) out[q * N + v] = __ldg(b + q * N + v) - acc[q];
+  }
+}
+
+// coarse[V] = sum over fine 2V + a, a in {-1,0,1}^3, of w(a) fine[2V + a] (R = I^T).
+__global__ void __launch_bounds__(256) k_restrict(const float* __restrict__ fine, int nf,
+                                                  float* __restrict__ coarse) {
+  const int nc = nf / 2;
+  const size_t Nf = static_cast<size_t>(nf) * nf * nf;
+  const size_t Nc = static_cast<size_t>(nc) * nc * nc;
+  for (size_t V = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; V < Nc;
+       V += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int X = static_cast<int>(V % nc), Y = static_cast<int>((V / nc) % nc),
+              Z = static_cast<int>(V / (static_cast<size_t>(nc) * nc));
+    const Nb nb = make_nb(2 * X, 2 * Y, 2 * Z, nf);
+    float acc[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const float w = (dx ? 0.5f : 1.f) * (dy ? 0.5f : 1.f) * (dz ? 0.5f : 1.f);
+      const size_t o = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+#pragma unroll
+      for (int q = 0; q < kPlanes; ++q) acc[q] = fmaf(w, __ldg(fine + q * Nf + o), acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) coarse[q * Nc + V] = acc[q];
+  }
+}
+
+// fine[v] (+)= sum of trilinear weights * coarse (I).
+__global__ void __launch_bounds__(256) k_prolong(const float* __restrict__ coarse, int nf,
+                                                 float* __restrict__ fine, int overwrite) {
+  const int nc = nf / 2;
+  const size_t Nf = static_cast<size_t>(nf) * nf * nf;
+  const size_t Nc = static_cast<size_t>(nc) * nc * nc;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < Nf;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(v % nf), y = static_cast<int>((v / nf) % nf),
+              z = static_cast<int>(v / (static_cast<size_t>(nf) * nf));
+    // the (up to) 8 coarse vertices around x/2; an even coordinate has one parent
+    const int x0 = x >> 1, y0 = y >> 1, z0 = z >> 1;
+    const int x1 = (x & 1) ? (x0 + 1 == nc ? 0 : x0 + 1) : x0;
+    const int y1 = (y & 1) ? (y0 + 1 == nc ? 0 : y0 + 1) : y0;
+    const int z1 = (z & 1) ? (z0 + 1 == nc ? 0 : z0 + 1) : z0;
+    size_t idx[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      idx[k] = static_cast<size_t>((k & 1) ? x1 : x0) +
+               static_cast<size_t>(nc) * (((k >> 1) & 1 ? y1 : y0) + static_cast<size_t>(nc) * ((k >> 2) ? z1 : z0));
+#pragma unroll 2
+    for (int q = 0; q < kPlanes; ++q) {
+      const float* cq = coarse + q * Nc;
+      float acc = 0.f;
+      // an axis with an even coordinate repeats its single parent in both corner slots,
+      // so each distinct parent appears 8 * (its trilinear weight) times among the 8
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc += __ldg(cq + idx[k]);
+      acc *= 0.125f;
+      fine[q * Nf + v] = overwrite ? acc : fine[q * Nf + v] + acc;
+    }
+  }
+}
+
+// Dense FP64 matrix of the coarsest stencil: A[3v+r][3w+c] = block (v, d)[r][c],
+// w = v + d wrapped (nc >= 3, so the 27 neighbours are distinct).
+__global__ void k_coarsest_dense(const float* __restrict__ st, int nc, bool cb,
+                                 double* __restrict__ A) {
+  const size_t Nc = static_cast<size_t>(nc) * nc * nc;
+  const int m = 3 * static_cast<int>(Nc);
+  for (size_t it = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; it < 27 * Nc;
+       it += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int d = static_cast<int>(it / Nc);
+    const size_t v = it - static_cast<size_t>(d) * Nc;
+    const int x = static_cast<int>(v % nc), y = static_cast<int>((v / nc) % nc),
+              z = static_cast<int>(v / (static_cast<size_t>(nc) * nc));
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    const size_t w = static_cast<size_t>((x + dx + nc) % nc) +
+                     static_cast<size_t>(nc) * (((y + dy + nc) % nc) + static_cast<size_t>(nc) * ((z + dz + nc) % nc));
+    const size_t p = stencil_pos(x, y, z, nc, cb);
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c)
+        A[(3 * v + r) * m + 3 * w + c] = static_cast<double>(st[static_cast<size_t>(9 * d + 3 * r + c) * Nc + p]);
+  }
+}
+
+// In-place Gauss-Jordan inverse of the SPD block A[3:, 3:] (vertex 0 pinned, Sec. 4.2
+// "eight corner vertices ... fixed"), no pivoting (SPD pivots are positive). One CTA.
+// Row and column 0..2 are zeroed, giving the pinned inverse embedded in m x m.
+__global__ void __launch_bounds__(1024) k_coarsest_invert(double* __restrict__ A, int m,
+                                                          int* __restrict__ status) {
+  __shared__ double piv_row[1536];
+  __shared__ double piv_col[1536];
+  for (int k = 3; k < m; ++k) {
+    const double piv = A[static_cast<size_t>(k) * m + k];
+    if (!(piv > 0.0)) {
+      if (threadIdx.x == 0) *status = 1;
+      return;
+    }
+    const double ip = 1.0 / piv;
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {
+      piv_row[j] = A[static_cast<size_t>(k) * m + j];
+      piv_col[j] = A[static_cast<size_t>(j) * m + k];
+    }
+    __syncthreads();
+    for (size_t e = threadIdx.x; e < static_cast<size_t>(m) * m; e += blockDim.x) {
+      const int i = static_cast<int>(e / m), j = static_cast<int>(e % m);
+      if (i < 3 || j < 3) continue;
+      double val;
+      if (i == k && j == k) val = ip;
+      else if (i == k) val = piv_row[j] * ip;
+      else if (j == k) val = -piv_col[i] * ip;
+      else val = A[e] - piv_col[i] * piv_row[j] * ip;
+      A[e] = val;
+    }
+    __syncthreads();
+  }
+  for (size_t e = threadIdx.x; e < static_cast<size_t>(m) * m; e += blockDim.x) {
+    const int i = static_cast<int>(e / m), j = static_cast<int>(e % m);
+    if (i < 3 || j < 3) A[e] = 0.0;
+  }
+}
+
+// G = P X P with P the projector removing the 3 rigid translations (per-component means):
+// the centred pseudo-inverse of the coarsest operator (Sec. 4.2 null-space removal).
+__global__ void __launch_bounds__(1024) k_coarsest_centre(const double* __restrict__ X, int m,
+                                                          double* __restrict__ G) {
+  extern __shared__ double sh[];          // rowmean[m*3] + tot[9]
+  double* rmean = sh;                     // rmean[i*3 + b] = mean_w X[i][3w+b]
+  double* tot = sh + 3 * m;
+  const int nv = m / 3;
+  for (int i = threadIdx.x; i < m; i += blockDim.x)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+      for (int w = 0; w < nv; ++w) s += X[static_cast<size_t>(i) * m + 3 * w + b];
+      rmean[i * 3 + b] = s / nv;
+    }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    const int a = threadIdx.x / 3, b = threadIdx.x % 3;
+    double s = 0.0;
+    for (int v = 0; v < nv; ++v) s += rmean[(3 * v + a) * 3 + b];
+    tot[threadIdx.x] = s / nv;
+  }
+  __syncthreads();
+  for (size_t e = threadIdx.x; e < static_cast<size_t>(m) * m; e += blockDim.x) {
+    const int i = static_cast<int>(e / m), j = static_cast<int>(e % m);
+    const int a = i % 3, b = j % 3;
+    // X symmetric: column mean of column j over rows of component a = rmean[j][a]
+    G[e] = X[e] - rmean[i * 3 + b] - rmean[j * 3 + a] + tot[a * 3 + b];
+  }
+}
+
+// x = G b for the 6 cases (FP64 dot products), one warp per output row.
+__global__ void __launch_bounds__(256) k_coarsest_apply(const double* __restrict__ G, int m,
+                                                        const float* __restrict__ b,
+                                                        float* __restrict__ x) {
+  const int nv = m / 3;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int row = warp; row < kCases * m; row += nwarps) {
+    const int c = row / m, i = row % m;
+    double s = 0.0;
+    for (int j = lane; j < m; j += 32) {
+      const int w = j / 3, k = j % 3;
+      s += G[static_cast<size_t>(i) * m + j] * static_cast<double>(b[static_cast<size_t>(3 * c + k) * nv + w]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) x[static_cast<size_t>(3 * c + i % 3) * nv + i / 3] = static_cast<float>(s);
+  }
+}
+
+// Export a stencil in vertex-major order out[(v*27 + d)*9 + q].
+__global__ void k_stencil_export(const float* __restrict__ st, int n, bool cb,
+                                 float* __restrict__ out) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t it = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; it < N * kStencil;
+       it += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = it / kStencil;
+    const int k = static_cast<int>(it % kStencil);
+    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
+              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
+    out[it] = st[static_cast<size_t>(k) * N + stencil_pos(x, y, z, n, cb)];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_level1_assemble(const homo_ctx* c, const Level& L1) {
+  // the 18 KB table travels in the kernel's parameter bank (limit 32 KB)
+  BfParam B;
+  for (int i = 0; i < 8 * 576; ++i) B.b[i] = c->hBf[i];
+  k_level1<<<grid_for(L1.N, 128), 128, 0, c->stream>>>(B, c->E, c->n, L1.st, L1.n, L1.colour_blocked);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, cudaStream_t s) {
+  k_galerkin<<<grid_for(27 * Lc.N, 256), 256, 0, s>>>(Lf.st, Lf.n, Lf.colour_blocked, Lc.st, Lc.n,
+                                                     Lc.colour_blocked);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_residual(const Level& L, const float* b, const float* x, float* out,
+                                   cudaStream_t s) {
+  k_coarse_residual<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, b, x, out, L.n, L.colour_blocked);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x,
+                             cudaStream_t s) {
+  const size_t h = static_cast<size_t>(L.n / 2);
+  k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.st, f, x, L.n, colour);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(int nf, const float* fine, float* coarse, cudaStream_t s) {
+  const size_t nc = static_cast<size_t>(nf / 2);
+  k_restrict<<<grid_for(nc * nc * nc, 256), 256, 0, s>>>(fine, nf, coarse);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(int nf, const float* coarse, float* fine, int overwrite,
+                               cudaStream_t s) {
+  const size_t Nf = static_cast<size_t>(nf) * nf * nf;
+  k_prolong<<<grid_for(Nf, 256), 256, 0, s>>>(coarse, nf, fine, overwrite);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarsest_setup(homo_ctx* c) {
+  const Level& L = c->lev[c->nlev - 1];
+  const int m = c->mc;
+  cudaError_t e = cudaMemsetAsync(c->A, 0, sizeof(double) * m * m, c->stream);
+  if (e != cudaSuccess) return e;
+  k_coarsest_dense<<<grid_for(27 * L.N, 256), 256, 0, c->stream>>>(L.st, L.n, L.colour_blocked, c->A);
+  int* status = reinterpret_cast<int*>(c->scal + S_OC + 63);
+  e = cudaMemsetAsync(status, 0, sizeof(int), c->stream);
+  if (e != cudaSuccess) return e;
+  k_coarsest_invert<<<1, 1024, 0, c->stream>>>(c->A, m, status);
+  const size_t shm = sizeof(double) * (3 * m + 9);
+  e = cudaFuncSetAttribute(k_coarsest_centre, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(shm));
+  if (e != cudaSuccess) return e;
+  k_coarsest_centre<<<1, 1024, shm, c->stream>>>(c->A, m, c->G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarsest_apply(const homo_ctx* c, const float* b, float* x) {
+  const int rows = kCases * c->mc;
+  const int blocks = (rows * 32 + 255) / 256;
+  k_coarsest_apply<<<blocks < 1216 ? blocks : 1216, 256, 0, c->stream>>>(c->G, c->mc, b, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_export(const Level& L, float* out, cudaStream_t s) {
+  k_stencil_export<<<grid_for(L.N * kStencil, 256), 256, 0, s>>>(L.st, L.n, L.colour_blocked, out);
+  return cudaGetLastError();
+}
+
+}  // namespace homo

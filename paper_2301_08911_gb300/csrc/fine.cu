@@ -1,0 +1,493 @@
+// Finest-level kernels. The level-0 stiffness is never stored (Sec. 4.1): every kernel
+// rebuilds what it needs from the element moduli E and the element matrix K0, which sits
+// in the kernel's parameter (constant) bank.
+//
+// Vertex form of K u (Eq. 13): incident element t = a + 2b + 4c of vertex v has origin
+// v - (1,1,1) + (a,b,c) and v is its local vertex 7 - t. The 3x3 coupling block between v
+// and its neighbour v + d is
+//     A_d = sum over (t, j) with bits(t) + bits(j) - 1 = d of E_t * K0[7 - t, j],
+// built once per vertex and applied to all 6 load cases (the 6 cases share E and K0).
+#include "dev_common.cuh"
+
+namespace homo {
+
+namespace {
+
+__device__ __forceinline__ void load_E8(const float* __restrict__ E, const Nb& nb, float (&Et)[8]) {
+#pragma unroll
+  for (int t = 0; t < 8; ++t) Et[t] = __ldg(E + nb.X[t & 1] + nb.Y[(t >> 1) & 1] + nb.Z[t >> 2]);
+}
+
+// 3x3 block A_d for neighbour offset (dx,dy,dz); all index arithmetic folds at compile
+// time once the callers' loops are unrolled.
+__device__ __forceinline__ void nb_block(const KeParam& K, const float (&Et)[8], int dx, int dy,
+                                         int dz, float (&A)[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) A[q] = 0.f;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int ja = dx + 1 - (t & 1), jb = dy + 1 - ((t >> 1) & 1), jc = dz + 1 - (t >> 2);
+    if (ja < 0 || ja > 1 || jb < 0 || jb > 1 || jc < 0 || jc > 1) continue;
+    const int j = ja + 2 * jb + 4 * jc, row = 7 - t;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        A[3 * r + c] = fmaf(Et[t], K.k[(3 * row + r) * 24 + 3 * j + c], A[3 * r + c]);
+  }
+}
+
+// Solve the SPD 3x3 system S y = b for 6 right-hand sides (LDL^T, FP32).
+__device__ __forceinline__ void solve3x6(const float (&S)[9], float (&b)[18]) {
+  const float d0 = S[0];
+  const float l10 = S[3] / d0, l20 = S[6] / d0;
+  const float d1 = S[4] - l10 * S[1];
+  const float l21 = (S[7] - l20 * S[1]) / d1;
+  const float d2 = S[8] - l20 * S[2] - l21 * (S[5] - l10 * S[2]);
+  const float i0 = 1.f / d0, i1 = 1.f / d1, i2 = 1.f / d2;
+#pragma unroll
+  for (int c = 0; c < kCases; ++c) {
+    float y0 = b[3 * c], y1 = b[3 * c + 1], y2 = b[3 * c + 2];
+    y1 -= l10 * y0;
+    y2 -= l20 * y0 + l21 * y1;
+    float x2 = y2 * i2;
+    float x1 = y1 * i1 - l21 * x2;
+    float x0 = y0 * i0 - l10 * x1 - l20 * x2;
+    b[3 * c] = x0;
+    b[3 * c + 1] = x1;
+    b[3 * c + 2] = x2;
+  }
+}
+
+// Modes: 0 out = K u; 1 out = K u in difference form, + optional partials of the dots
+//        (u_c, out_c) and of the 18 plane sums of out; 3 out = b - K u.
+// The difference form uses sum_d A_d = 0 (rows of K annihilate translations) to apply
+// K to u_(v+d) - u_v, so large smooth fields lose no precision to cancellation.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fine_apply(const __grid_constant__ KeParam K,
+                                                    const float* __restrict__ E,
+                                                    const float* __restrict__ u,
+                                                    const float* __restrict__ ulo,
+                                                    const float* __restrict__ b,
+                                                    float* __restrict__ out, int n,
+                                                    double* __restrict__ part) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  float red[kCases + kPlanes];
+#pragma unroll
+  for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
+              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    float acc[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
+    float own[kPlanes];
+    if (MODE == 1) {
+#pragma unroll
+      for (int q = 0; q < kPlanes; ++q) own[q] = __ldg(u + q * N + v);
+    }
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      if (MODE == 1 && d == 13) continue;
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      float A[9];
+      nb_block(K, Et, dx, dy, dz, A);
+      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+#pragma unroll
+      for (int c = 0; c < kCases; ++c) {
+        float uu[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const size_t o = static_cast<size_t>(3 * c + k) * N + w;
+          if (MODE == 1) uu[k] = __ldg(u + o) - own[3 * c + k];
+          else uu[k] = __ldg(u + o);
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          acc[3 * c + r] = fmaf(A[3 * r], uu[0], fmaf(A[3 * r + 1], uu[1], fmaf(A[3 * r + 2], uu[2], acc[3 * c + r])));
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCases; ++c)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const size_t o = static_cast<size_t>(3 * c + k) * N + v;
+        float val = acc[3 * c + k];
+        if (MODE == 3) val = __ldg(b + o) - val;
+        out[o] = val;
+        if (MODE == 1) {
+          red[c] = fmaf(own[3 * c + k], val, red[c]);
+          red[kCases + 3 * c + k] += val;
+        }
+      }
+  }
+  if (MODE == 1 && part != nullptr) block_sum_store<kCases + kPlanes>(red, part);
+}
+
+// One colour pass of 8-colour block Gauss-Seidel (Eq. 15-16): for every vertex v of
+// the colour, S_v u_v = f_v - M_v with S_v = A_0 and M_v = sum_(d != 0) A_d u_(v+d).
+__global__ void __launch_bounds__(256) k_fine_gs(const __grid_constant__ KeParam K,
+                                                 const float* __restrict__ E,
+                                                 const float* __restrict__ f,
+                                                 float* __restrict__ u, int n, int colour) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  const int h = n >> 1;
+  const size_t Nh = static_cast<size_t>(h) * h * h;
+  const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
+  for (size_t m = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < Nh;
+       m += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = 2 * static_cast<int>(m % h) + cx;
+    const int y = 2 * static_cast<int>((m / h) % h) + cy;
+    const int z = 2 * static_cast<int>(m / (static_cast<size_t>(h) * h)) + cz;
+    const size_t v = static_cast<size_t>(x) + static_cast<size_t>(n) * (y + static_cast<size_t>(n) * z);
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    float rhs[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) rhs[q] = __ldg(f + q * N + v);
+    float S[9];
+    nb_block(K, Et, 0, 0, 0, S);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      if (d == 13) continue;
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      float A[9];
+      nb_block(K, Et, dx, dy, dz, A);
+      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+#pragma unroll
+      for (int c = 0; c < kCases; ++c) {
+        const float u0 = u[(3 * c) * N + w], u1 = u[(3 * c + 1) * N + w], u2 = u[(3 * c + 2) * N + w];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          rhs[3 * c + r] -= fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, A[3 * r + 2] * u2));
+      }
+    }
+    solve3x6(S, rhs);
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) u[q * N + v] = rhs[q];
+  }
+}
+
+// Macro-strain loads in vertex form (Eq. 11): f_(i,v) = sum_t E_t (K0 chi_i)[7 - t].
+// In a uniform medium the 8 element forces at a vertex cancel exactly (sum_t (K0
+// chi_i)[7 - t] = 0), so the kernel sums (E_t - E_0) (K0 chi_i)[7 - t]: the loads are
+// exactly zero where E is locally uniform and carry no cancellation error elsewhere.
+__global__ void __launch_bounds__(256) k_loads(const __grid_constant__ LoadParam L,
+                                               const float* __restrict__ E,
+                                               float* __restrict__ f, int n) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
+              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    float dE[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) dE[t] = Et[t] - Et[0];
+#pragma unroll
+    for (int c = 0; c < kCases; ++c)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int t = 1; t < 8; ++t) s = fmaf(dE[t], L.fe[c][3 * (7 - t) + r], s);
+        f[static_cast<size_t>(3 * c + r) * N + v] = s;
+      }
+  }
+}
+
+// Error-free transformations (Knuth TwoSum, FMA-based TwoProduct) with operations the
+// compiler may not contract or reorder.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fadd_rn(s, -a);
+  e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+}
+
+// r = b - K (u + ulo) evaluated in double-float arithmetic (difference form, products
+// and sums error-free up to the final rounding), then partials of ||r_c||^2 and of the
+// 18 plane sums. This is the accurate true residual the CG driver restarts from; it uses
+// exactly the FP32 blocks A_d of the CG product, so both see the same operator.
+__global__ void __launch_bounds__(128) k_fine_true_residual(const __grid_constant__ KeParam K,
+                                                            const float* __restrict__ E,
+                                                            const float* __restrict__ u,
+                                                            const float* __restrict__ ulo,
+                                                            const float* __restrict__ b,
+                                                            float* __restrict__ out, int n,
+                                                            double* __restrict__ part) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  float red[kCases + kPlanes];
+#pragma unroll
+  for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
+              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    float hi[kPlanes], lo[kPlanes], own[kPlanes], ownlo[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) {
+      hi[q] = 0.f;
+      lo[q] = 0.f;
+      own[q] = __ldg(u + q * N + v);
+      ownlo[q] = __ldg(ulo + q * N + v);
+    }
+#pragma unroll 1
+    for (int d = 0; d < 27; ++d) {
+      if (d == 13) continue;
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      float A[9];
+      // runtime d: the block is rebuilt with runtime offsets (same FP32 operations and
+      // order as the compile-time version in the CG product)
+      nb_block(K, Et, dx, dy, dz, A);
+      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+#pragma unroll
+      for (int c = 0; c < kCases; ++c) {
+        float dh[3], dl[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const size_t o = static_cast<size_t>(3 * c + k) * N + w;
+          float e;
+          two_sum(__ldg(u + o), -own[3 * c + k], dh[k], e);
+          dl[k] = __fadd_rn(e, __fadd_rn(__ldg(ulo + o), -ownlo[3 * c + k]));
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const float a = A[3 * r + k];
+            const float p = __fmul_rn(a, dh[k]);
+            const float pe = fmaf(a, dh[k], -p);
+            float s, e;
+            two_sum(hi[3 * c + r], p, s, e);
+            hi[3 * c + r] = s;
+            lo[3 * c + r] = __fadd_rn(lo[3 * c + r], __fadd_rn(e, fmaf(a, dl[k], pe)));
+          }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) {
+      const size_t o = static_cast<size_t>(q) * N + v;
+      float s, e;
+      two_sum(__ldg(b + o), -hi[q], s, e);
+      const float val = __fadd_rn(s, __fadd_rn(e, -lo[q]));
+      out[o] = val;
+      red[q / 3] = fmaf(val, val, red[q / 3]);
+      red[kCases + q] += val;
+    }
+  }
+  block_sum_store<kCases + kPlanes>(red, part);
+}
+
+// Level-0 stencil written out (used only when the finest level is also the coarsest and
+// is solved directly): st[(9d + q) * N + pos(v)] = A_d[q].
+__global__ void __launch_bounds__(256) k_fine_stencil(const __grid_constant__ KeParam K,
+                                                      const float* __restrict__ E, int n, bool cb,
+                                                      float* __restrict__ st) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
+              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    const size_t p = stencil_pos(x, y, z, n, cb);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      float A[9];
+      nb_block(K, Et, d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1, A);
+#pragma unroll
+      for (int q = 0; q < 9; ++q) st[static_cast<size_t>(9 * d + q) * N + p] = A[q];
+    }
+  }
+}
+
+__global__ void k_simp(const float* __restrict__ rin, float* __restrict__ rout,
+                       float* __restrict__ E, size_t N, float p, float E0, float Emin) {
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    float r = rin[e];
+    r = fminf(fmaxf(r, 0.f), 1.f);
+    rout[e] = r;
+    E[e] = Emin + powf(r, p) * (E0 - Emin);
+  }
+}
+
+struct ElemParam {
+  float gsym[21];   // objective gradient folded onto the 21 (i <= j) pairs
+  float p, dE;      // SIMP exponent, E0 - Emin
+  float invN;
+};
+
+constexpr int kElemBlock = 128;
+constexpr int kElemStride = 165;   // 144 w values + 21 products per thread row (odd: bank spread)
+
+// Per element q_ij = w_i^T K0 w_j, w_i = chi_i - (u_i - u_i at local vertex 0): the
+// summand of Eq. 7 (subtracting the element's own translation leaves K0 w unchanged and
+// keeps FP32 round-off independent of the field's magnitude, cf. Sec. 4.2 "relative
+// coordinate"). MODE 0: block partial sums of E_e q_ij (21 values, Kahan-compensated
+// per thread). MODE 1: sensitivity (Eq. 8-9) p rho^(p-1) dE sum_ij g_ij q_ij / N.
+template <int MODE>
+__global__ void __launch_bounds__(kElemBlock) k_fine_elem(const __grid_constant__ KeParam K,
+                                                          const __grid_constant__ ChiParam X,
+                                                          const __grid_constant__ ElemParam P,
+                                                          const float* __restrict__ E,
+                                                          const float* __restrict__ rho,
+                                                          const float* __restrict__ u,
+                                                          const float* __restrict__ ulo, int n,
+                                                          float* __restrict__ sens,
+                                                          double* __restrict__ part) {
+  extern __shared__ float wsh[];
+  float* w = wsh + threadIdx.x * kElemStride;
+  const size_t N = static_cast<size_t>(n) * n * n;
+  float cs[21], cc[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) cs[k] = cc[k] = 0.f;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(e % n), y = static_cast<int>((e / n) % n),
+              z = static_cast<int>(e / (static_cast<size_t>(n) * n));
+    const int xs[2] = {x, x == n - 1 ? 0 : x + 1};
+    const int ys[2] = {y * n, (y == n - 1 ? 0 : y + 1) * n};
+    const int zs[2] = {z * n * n, (z == n - 1 ? 0 : z + 1) * n * n};
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) {
+      const float* uq = u + static_cast<size_t>(q) * N;
+      const float* lq = ulo + static_cast<size_t>(q) * N;
+      const float h0 = __ldg(uq + e), l0 = __ldg(lq + e);
+      const int c = q / 3, k = q % 3;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t vj = static_cast<size_t>(xs[j & 1] + ys[(j >> 1) & 1] + zs[j >> 2]);
+        const float du = (__ldg(uq + vj) - h0) + (__ldg(lq + vj) - l0);
+        w[c * 24 + 3 * j + k] = X.chi[c][3 * j + k] - du;
+      }
+    }
+    float* q = w + 144;   // 21 products, (i, j >= i) row-major
+#pragma unroll 1
+    for (int i = 0, idx = 0; i < kCases; ++i) {
+      float yv[24];
+#pragma unroll
+      for (int r = 0; r < 24; ++r) yv[r] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 24; ++k) {
+        const float wk = w[i * 24 + k];
+#pragma unroll
+        for (int r = 0; r < 24; ++r) yv[r] = fmaf(K.k[r * 24 + k], wk, yv[r]);
+      }
+#pragma unroll 1
+      for (int j = i; j < kCases; ++j, ++idx) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) s = fmaf(yv[k], w[j * 24 + k], s);
+        q[idx] = s;
+      }
+    }
+    if (MODE == 0) {
+      const float Ee = __ldg(E + e);
+#pragma unroll
+      for (int k = 0; k < 21; ++k) {   // Kahan summation of E_e q_e,k
+        const float yk = fmaf(Ee, q[k], -cc[k]);
+        const float t = cs[k] + yk;
+        cc[k] = (t - cs[k]) - yk;
+        cs[k] = t;
+      }
+    } else {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < 21; ++k) s = fmaf(P.gsym[k], q[k], s);
+      const float r = __ldg(rho + e);
+      sens[e] = P.p * powf(r, P.p - 1.f) * P.dE * s * P.invN;
+    }
+  }
+  if (MODE == 0) block_sum_store<21>(cs, part);
+}
+
+}  // namespace
+
+cudaError_t launch_simp(const float* rho_in, float* rho_out, float* E, size_t N, float p,
+                        float E0, float Emin, cudaStream_t s) {
+  k_simp<<<grid_for(N, 256), 256, 0, s>>>(rho_in, rho_out, E, N, p, E0, Emin);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_stencil(const homo_ctx* c, const Level& L0) {
+  k_fine_stencil<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->ke, c->E, c->n, L0.colour_blocked, L0.st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_loads(const homo_ctx* c, float* f) {
+  k_loads<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->ld, c->E, f, c->n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, int diff,
+                              double* part, int* grid_out) {
+  const int g = grid_for(c->N, 256);
+  if (grid_out) *grid_out = g;
+  if (diff)
+    k_fine_apply<1><<<g, 256, 0, c->stream>>>(c->ke, c->E, u, nullptr, nullptr, out, c->n, part);
+  else
+    k_fine_apply<0><<<g, 256, 0, c->stream>>>(c->ke, c->E, u, nullptr, nullptr, out, c->n, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float* u,
+                                 const float* ulo, float* out, double* part, int* grid_out) {
+  if (ulo) {
+    const int g = grid_for(c->N, 128);
+    if (grid_out) *grid_out = g;
+    k_fine_true_residual<<<g, 128, 0, c->stream>>>(c->ke, c->E, u, ulo, b, out, c->n, part);
+  } else {
+    const int g = grid_for(c->N, 256);
+    if (grid_out) *grid_out = g;
+    k_fine_apply<3><<<g, 256, 0, c->stream>>>(c->ke, c->E, u, nullptr, b, out, c->n, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u) {
+  const size_t h = static_cast<size_t>(c->n / 2);
+  k_fine_gs<<<grid_for(h * h * h, 256), 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, float* sens,
+                             double* part, int* grid_out) {
+  ElemParam P{};
+  if (g36) {
+    int idx = 0;
+    for (int i = 0; i < kCases; ++i)
+      for (int j = i; j < kCases; ++j)
+        P.gsym[idx++] = static_cast<float>(i == j ? g36[6 * i + j] : g36[6 * i + j] + g36[6 * j + i]);
+  }
+  P.p = static_cast<float>(c->p);
+  P.dE = static_cast<float>(c->E0 - c->Emin);
+  P.invN = static_cast<float>(1.0 / static_cast<double>(c->N));
+  const int g = grid_for(c->N, kElemBlock);
+  if (grid_out) *grid_out = g;
+  const size_t shm = static_cast<size_t>(kElemBlock) * kElemStride * sizeof(float);
+  cudaError_t ae = cudaFuncSetAttribute(mode == 0 ? k_fine_elem<0> : k_fine_elem<1>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        static_cast<int>(shm));
+  if (ae != cudaSuccess) return ae;
+  if (mode == 0)
+    k_fine_elem<0><<<g, kElemBlock, shm, c->stream>>>(c->ke, c->chi, P, c->E, c->rho, c->u, c->ulo,
+                                                     c->n, sens, part);
+  else
+    k_fine_elem<1><<<g, kElemBlock, shm, c->stream>>>(c->ke, c->chi, P, c->E, c->rho, c->u, c->ulo,
+                                                     c->n, sens, part);
+  return cudaGetLastError();
+}
+
+}  // namespace homo

@@ -1,0 +1,204 @@
+// Internal declarations of the homo library (not part of the C ABI).
+//
+// Data layout on the device (voxel units, element side 1):
+//   * scalar element fields (rho~, E): N = n^3 floats, x fastest.
+//   * 6-case vector fields: 18 planes of N floats, plane = 3*case + comp.
+//   * level l >= 1 Galerkin stencils: 243 planes of N_l floats, plane = 9*d + 3*r + c
+//     (d = neighbour offset (dx+1)+3(dy+1)+9(dz+1), 3x3 block row r, column c); inside
+//     a plane the vertices are grouped by Gauss-Seidel colour (Sec. 4.1 "Memory
+//     layouts") when n_l is even, so one colour pass reads one contiguous 1/8 of every
+//     plane; x-fastest order when n_l is odd (only possible on the coarsest level).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "homo.h"
+
+namespace homo {
+
+constexpr int kCases = 6;
+constexpr int kPlanes = 18;
+constexpr int kStencil = 243;
+constexpr int kMaxLevels = 16;
+constexpr int kRedBlock = 256;          // threads per block of every reduction kernel
+constexpr int kOcPasses = 8;            // OC multiplier search passes (15 candidates each)
+constexpr int kOcKernels = 4 + 3 * kOcPasses;   // kernels one OC update launches
+
+// Element matrix of a unit-modulus voxel (side 1), row-major 24x24, dof 3j + comp.
+struct KeParam {
+  float k[576];
+};
+
+// Per-case nodal force of a unit-modulus element under the unit macro strain:
+// fe[i][3j+comp] = (K0 chi_i)[3j+comp] (Eq. 4 with the element-relative chi of Eq. 12).
+struct LoadParam {
+  float fe[kCases][24];
+};
+
+// Element-relative unit-strain displacements chi_i (Eq. 12), voxel units.
+struct ChiParam {
+  float chi[kCases][24];
+};
+
+// Filter weights (periodic linear cone) for up to 7^3 offsets.
+struct FilterParam {
+  int count;
+  float inv_wsum;
+  signed char off[343][3];
+  float w[343];
+};
+
+struct Level {
+  int n = 0;
+  size_t N = 0;
+  bool colour_blocked = false;
+  float* st = nullptr;   // 243 * N (levels >= 1)
+  float* x = nullptr;    // 18 * N (levels >= 1)
+  float* b = nullptr;    // 18 * N (levels >= 1)
+  float* t = nullptr;    // 18 * N residual scratch (levels >= 1)
+};
+
+// Device-side scalar slots (doubles) used by the CG driver.
+// Pairs reduced by one kernel are contiguous (6 dots followed by 18 plane sums).
+enum Slot : int {
+  S_FF = 0,        // ||f_c||^2                  [6]
+  S_RR = 6,        // ||r_c||^2                  [6]
+  S_RSUM = 12,     // sum of r per plane         [18]
+  S_RZ = 30,       // (r_c, z_c)                 [6]
+  S_ZSUM = 36,     // sum of z per plane         [18]
+  S_RZ_OLD = 54,   // previous (r_c, z_c)        [6]
+  S_PQ = 60,       // (p_c, K p_c)               [6]
+  S_QSUM = 66,     // sum of K p per plane       [18]
+  S_ALPHA = 84,    // alpha_c                    [6]
+  S_BETA = 90,     // beta_c                     [6]
+  S_ACTIVE = 96,   // 1.0 while case c iterates  [6]
+  S_CH = 102,      // C^H sums                   [21]
+  S_OC = 128,      // OC scratch                 [64]
+  S_COUNT = 192
+};
+
+struct homo_ctx_impl;
+
+}  // namespace homo
+
+struct homo_ctx {
+  int n = 0;
+  size_t N = 0;
+  double E0 = 1, nu = 0.3, p = 3, Emin = 1e-9;
+  homo_opts opts{};
+  cudaStream_t stream = nullptr;
+  homo::KeParam ke{};
+  homo::LoadParam ld{};
+  homo::ChiParam chi{};
+
+  float* rho = nullptr;      // filtered density, N
+  float* E = nullptr;        // element moduli, N
+  float* u = nullptr;        // displacement, 18N (high part)
+  float* ulo = nullptr;      // displacement low part (u = u + ulo exactly), 18N
+  float* f = nullptr;        // loads, 18N
+  float* r = nullptr;        // CG residual, 18N
+  float* z = nullptr;        // preconditioned residual, 18N
+  float* pv = nullptr;       // CG direction, 18N
+  float* q = nullptr;        // K p and V-cycle level-0 residual scratch, 18N
+  float* tmp = nullptr;      // N floats scratch (OC)
+
+  int nlev = 0;
+  homo::Level lev[homo::kMaxLevels];
+  std::vector<float> hBf;    // level-1 Galerkin tables (host), 8 * 576 floats
+  int nc = 0, mc = 0;        // coarsest cells per axis, 3*nc^3
+  double* A = nullptr;       // mc*mc FP64 work (coarsest)
+  double* G = nullptr;       // mc*mc FP64 centred pseudo-inverse of the coarsest operator
+
+  double* part = nullptr;    // reduction partials
+  size_t part_cap = 0;       // doubles
+  double* scal = nullptr;    // device slots (homo::Slot)
+  double* hscal = nullptr;   // pinned host mirror of scal
+
+  bool loads_valid = false, hier_valid = false, solved = false, density_set = false;
+  std::string err;
+
+  // measurement: launch counter and optional per-class event timing
+  struct ProfRec {
+    int kc;
+    cudaEvent_t a, b;
+  };
+  long long launches = 0;
+  bool prof = false;
+  std::vector<ProfRec> pending;
+  std::vector<cudaEvent_t> event_pool;
+  long long prof_n[HOMO_KC_COUNT] = {};
+  double prof_ms[HOMO_KC_COUNT] = {};
+
+  // relative residual of the 6 cases after every CG iteration of the last solve
+  std::vector<double> history;
+};
+
+namespace homo {
+
+// ---- host helpers (element.cu) ----
+void build_element_matrix(double nu, KeParam& ke, LoadParam& ld, ChiParam& chi);
+void build_level1_tables(const KeParam& ke, float* host_Bf /* 8*576 */);
+int build_filter_param(double radius, FilterParam& fp);
+
+// ---- launchers (fine.cu) ----
+cudaError_t launch_simp(const float* rho_in, float* rho_out, float* E, size_t N, float p,
+                        float E0, float Emin, cudaStream_t s);
+cudaError_t launch_loads(const homo_ctx* c, float* f);
+// out = K u (diff form if diff != 0) on level 0; if pq != nullptr also block partials of
+// (u_c, out_c) into part (grid * 6 doubles) and returns the grid size in *grid_out.
+cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, int diff,
+                              double* part, int* grid_out);
+// out = b - K (u + ulo) in difference form (accurate true residual); partials of ||out_c||^2.
+cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float* u,
+                                 const float* ulo, float* out, double* part, int* grid_out);
+cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u);
+cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, float* sens,
+                             double* part, int* grid_out);
+
+// ---- launchers (coarse.cu) ----
+cudaError_t launch_level1_assemble(const homo_ctx* c, const Level& L1);
+cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, cudaStream_t s);
+cudaError_t launch_coarse_residual(const Level& L, const float* b, const float* x, float* out,
+                                   cudaStream_t s);
+cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x,
+                             cudaStream_t s);
+cudaError_t launch_restrict(int nf, const float* fine, float* coarse, cudaStream_t s);
+cudaError_t launch_prolong_add(int nf, const float* coarse, float* fine, int overwrite,
+                               cudaStream_t s);
+cudaError_t launch_coarsest_setup(homo_ctx* c);
+cudaError_t launch_coarsest_apply(const homo_ctx* c, const float* b, float* x);
+cudaError_t launch_stencil_export(const Level& L, float* out, cudaStream_t s);
+// level-0 stencil (243 planes, colour-blocked when n is even) built from E and K0
+cudaError_t launch_fine_stencil(const homo_ctx* c, const Level& L0);
+
+// ---- launchers (vec.cu) ----
+int reduce_grid(size_t n_items);
+cudaError_t launch_sum_partials(const double* part, int nblk, int nv, double* out,
+                                cudaStream_t s);
+cudaError_t launch_dot6(const float* a, const float* b, size_t N, double* part, int* grid_out,
+                        cudaStream_t s);
+cudaError_t launch_dot6_zsum(const float* r, const float* z, size_t N, double* part,
+                             int* grid_out, cudaStream_t s);
+cudaError_t launch_cg_alpha(double* scal, cudaStream_t s);
+cudaError_t launch_cg_beta(double* scal, int first, cudaStream_t s);
+cudaError_t launch_cg_active(double* scal, double tol, int centre, size_t N, cudaStream_t s);
+cudaError_t launch_center(float* r, const double* scal, size_t N, cudaStream_t s);
+cudaError_t launch_cg_update_xr(float* u, float* ulo, float* r, const float* p, const float* q,
+                                const double* scal, size_t N, double* part, int* grid_out,
+                                cudaStream_t s);
+cudaError_t launch_cg_update_p(float* p, const float* z, const double* scal, size_t N,
+                               cudaStream_t s);
+cudaError_t launch_split_set(float* hi, float* lo, const float* src, size_t n, cudaStream_t s);
+cudaError_t launch_split_get(const float* hi, const float* lo, float* dst, size_t n,
+                             cudaStream_t s);
+cudaError_t launch_filter(const FilterParam& fp, int n, const float* in, float* out,
+                          cudaStream_t s);
+cudaError_t launch_oc(homo_ctx* c, const float* dc, float* rho, double volfrac, double move,
+                      double eta, double rho_min, double* change);
+
+}  // namespace homo

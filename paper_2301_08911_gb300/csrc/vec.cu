@@ -1,0 +1,493 @@
+// Vector kernels of the CG driver, reductions, the periodic density filter and the OC
+// update. All reductions are two-stage and deterministic: per-block partials in FP64,
+// then one block sums them in a fixed order.
+#include <cmath>
+
+#include "dev_common.cuh"
+
+namespace homo {
+
+namespace {
+
+__global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ part, int nblk,
+                                                      int nv, double* __restrict__ out) {
+  __shared__ double sh[256];
+  for (int k = 0; k < nv; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[static_cast<size_t>(b) * nv + k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = sh[0];
+    __syncthreads();
+  }
+}
+
+// Per case c: sum over the 3 planes of case c of a*b.
+__global__ void __launch_bounds__(256) k_dot6(const float* __restrict__ a,
+                                              const float* __restrict__ b, size_t N,
+                                              double* __restrict__ part) {
+  float red[kCases];
+#pragma unroll
+  for (int c = 0; c < kCases; ++c) red[c] = 0.f;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) red[q / 3] = fmaf(__ldg(a + q * N + v), __ldg(b + q * N + v), red[q / 3]);
+  }
+  block_sum_store<kCases>(red, part);
+}
+
+// (r_c, z_c) for the 6 cases and the 18 plane sums of z (for removing the mean).
+__global__ void __launch_bounds__(256) k_dot6_zsum(const float* __restrict__ r,
+                                                   const float* __restrict__ z, size_t N,
+                                                   double* __restrict__ part) {
+  float red[kCases + kPlanes];
+#pragma unroll
+  for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) {
+      const float zz = __ldg(z + q * N + v);
+      red[q / 3] = fmaf(__ldg(r + q * N + v), zz, red[q / 3]);
+      red[kCases + q] += zz;
+    }
+  }
+  block_sum_store<kCases + kPlanes>(red, part);
+}
+
+__global__ void k_cg_alpha(double* __restrict__ s) {
+  const int c = threadIdx.x;
+  if (c >= kCases) return;
+  const double pq = s[S_PQ + c];
+  double a = 0.0;
+  if (s[S_ACTIVE + c] != 0.0 && pq > 0.0 && isfinite(pq)) a = s[S_RZ + c] / pq;
+  s[S_ALPHA + c] = a;
+}
+
+// beta = rz_new / rz_old (0 on the first step or for finished cases); rz_old <- rz_new.
+__global__ void k_cg_beta(double* __restrict__ s, int first) {
+  const int c = threadIdx.x;
+  if (c >= kCases) return;
+  const double rz = s[S_RZ + c], old = s[S_RZ_OLD + c];
+  double b = 0.0;
+  if (!first && s[S_ACTIVE + c] != 0.0 && old != 0.0 && isfinite(rz)) b = rz / old;
+  s[S_BETA + c] = b;
+  s[S_RZ_OLD + c] = rz;
+}
+
+// Case c keeps iterating while ||r_c||^2 > tol^2 ||f_c||^2. With centre != 0 the residual
+// has just had its plane means removed: ||r_c||^2 loses N * mean^2 per plane.
+__global__ void k_cg_active(double* __restrict__ s, double tol2, int centre, double N) {
+  const int c = threadIdx.x;
+  if (c >= kCases) return;
+  double rr = s[S_RR + c];
+  if (centre) {
+    for (int k = 0; k < 3; ++k) rr -= s[S_RSUM + 3 * c + k] * s[S_RSUM + 3 * c + k] / N;
+    rr = fmax(rr, 0.0);
+    s[S_RR + c] = rr;
+  }
+  const double ff = s[S_FF + c];
+  s[S_ACTIVE + c] = (ff > 0.0 && rr > tol2 * ff) ? 1.0 : 0.0;
+}
+
+// r -= mean(r) per plane (the rigid-translation component, which K cannot produce).
+__global__ void __launch_bounds__(256) k_center(float* __restrict__ r, const double* __restrict__ s,
+                                                size_t N) {
+  float m[kPlanes];
+#pragma unroll
+  for (int k = 0; k < kPlanes; ++k) m[k] = static_cast<float>(s[S_RSUM + k] / static_cast<double>(N));
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kPlanes; ++k) r[static_cast<size_t>(k) * N + v] -= m[k];
+  }
+}
+
+// u (+ ulo) += alpha p in double-float arithmetic (error-free transformations with
+// non-contracted operations), r -= alpha (q - mean q), partial sums of ||r_c||^2 and of
+// the 18 plane sums of r.
+__global__ void __launch_bounds__(256) k_cg_update_xr(float* __restrict__ u, float* __restrict__ ulo,
+                                                      float* __restrict__ r,
+                                                      const float* __restrict__ p,
+                                                      const float* __restrict__ q,
+                                                      const double* __restrict__ s, size_t N,
+                                                      double* __restrict__ part) {
+  float a[kCases];
+#pragma unroll
+  for (int c = 0; c < kCases; ++c) a[c] = static_cast<float>(s[S_ALPHA + c]);
+  float red[kCases + kPlanes], qm[kPlanes];
+#pragma unroll
+  for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kPlanes; ++k) qm[k] = static_cast<float>(s[S_QSUM + k] / static_cast<double>(N));
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kPlanes; ++k) {
+      const int c = k / 3;
+      const size_t o = static_cast<size_t>(k) * N + v;
+      float rv = r[o];
+      if (a[c] != 0.f) {
+        const float pv = p[o];
+        const float pa = __fmul_rn(a[c], pv);
+        const float pe = fmaf(a[c], pv, -pa);            // exact product error
+        const float hi = u[o];
+        const float sm = __fadd_rn(hi, pa);              // TwoSum(hi, pa)
+        const float bb = __fadd_rn(sm, -hi);
+        const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(sm, -bb)), __fadd_rn(pa, -bb));
+        const float lo = __fadd_rn(__fadd_rn(ulo[o], e), pe);
+        const float s2 = __fadd_rn(sm, lo);              // FastTwoSum renormalisation
+        u[o] = s2;
+        ulo[o] = __fadd_rn(lo, -__fadd_rn(s2, -sm));
+        rv = fmaf(-a[c], q[o] - qm[k], rv);
+        r[o] = rv;
+      }
+      red[c] = fmaf(rv, rv, red[c]);
+      red[kCases + k] += rv;
+    }
+  }
+  block_sum_store<kCases + kPlanes>(red, part);
+}
+
+// p = (z - mean(z)) + beta p per plane.
+__global__ void __launch_bounds__(256) k_cg_update_p(float* __restrict__ p,
+                                                     const float* __restrict__ z,
+                                                     const double* __restrict__ s, size_t N) {
+  float b[kCases], mz[kPlanes];
+#pragma unroll
+  for (int c = 0; c < kCases; ++c) b[c] = static_cast<float>(s[S_BETA + c]);
+#pragma unroll
+  for (int k = 0; k < kPlanes; ++k) mz[k] = static_cast<float>(s[S_ZSUM + k] / static_cast<double>(N));
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < kPlanes; ++k) {
+      const size_t o = static_cast<size_t>(k) * N + v;
+      const float zz = __ldg(z + o) - mz[k];
+      p[o] = b[k / 3] != 0.f ? fmaf(b[k / 3], p[o], zz) : zz;
+    }
+  }
+}
+
+__global__ void k_split_set(float* __restrict__ hi, float* __restrict__ lo,
+                            const float* __restrict__ src, size_t n) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    hi[i] = src[i];
+    lo[i] = 0.f;
+  }
+}
+
+__global__ void k_split_get(const float* __restrict__ hi, const float* __restrict__ lo,
+                            float* __restrict__ dst, size_t n) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x)
+    dst[i] = hi[i] + lo[i];
+}
+
+// Periodic linear-cone filter: out_e = inv_wsum * sum_k w_k in_(e + off_k).
+__global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterParam F, int n,
+                                                const float* __restrict__ in,
+                                                float* __restrict__ out) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(e % n), y = static_cast<int>((e / n) % n),
+              z = static_cast<int>(e / (static_cast<size_t>(n) * n));
+    float s = 0.f;
+    for (int k = 0; k < F.count; ++k) {
+      int xx = x + F.off[k][0], yy = y + F.off[k][1], zz = z + F.off[k][2];
+      xx += xx < 0 ? n : (xx >= n ? -n : 0);
+      yy += yy < 0 ? n : (yy >= n ? -n : 0);
+      zz += zz < 0 ? n : (zz >= n ? -n : 0);
+      s = fmaf(F.w[k], __ldg(in + xx + static_cast<size_t>(n) * (yy + static_cast<size_t>(n) * zz)), s);
+    }
+    out[e] = s * F.inv_wsum;
+  }
+}
+
+// ---------------------------------------------------------------- OC update
+// rho_new(s) = clamp(base_e * s, lo_e, hi_e), base_e = rho_e max(-dc_e, 0)^eta,
+// s = lambda^(-eta); mean(rho_new) increases with s. OC scratch (doubles at S_OC):
+constexpr int kOcCand = 15;      // candidate multipliers per pass
+// kOcPasses passes (homo_internal.cuh): the bracket shrinks 16x per pass in log scale
+enum { OC_SLO = 0, OC_SHI = 1, OC_MODE = 2, OC_CAND = 8, OC_CHANGE = 32, OC_SUMS = 40 };
+
+__device__ __forceinline__ float oc_lo(float r, float move, float rmin) { return fmaxf(rmin, r - move); }
+__device__ __forceinline__ float oc_hi(float r, float move) { return fminf(1.f, r + move); }
+
+// base -> tmp; block partials [min lo/base, max hi/base, sum lo, sum hi] over base > 0.
+__global__ void __launch_bounds__(256) k_oc_setup(const float* __restrict__ rho,
+                                                  const float* __restrict__ dc,
+                                                  float* __restrict__ base, size_t N, float eta,
+                                                  float move, float rmin,
+                                                  double* __restrict__ part) {
+  float mn = INFINITY, mx = 0.f;
+  double slo = 0.0, shi = 0.0;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const float r = rho[e];
+    const float D = fmaxf(-dc[e], 0.f);
+    const float bs = D > 0.f ? r * powf(D, eta) : 0.f;
+    base[e] = bs;
+    const float lo = oc_lo(r, move, rmin), hi = oc_hi(r, move);
+    slo += lo;
+    shi += hi;
+    if (bs > 0.f) {
+      mn = fminf(mn, lo / bs);
+      mx = fmaxf(mx, hi / bs);
+    }
+  }
+  __shared__ float smn[256], smx[256];
+  __shared__ double ssl[256], ssh[256];
+  smn[threadIdx.x] = mn;
+  smx[threadIdx.x] = mx;
+  ssl[threadIdx.x] = slo;
+  ssh[threadIdx.x] = shi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smn[threadIdx.x] = fminf(smn[threadIdx.x], smn[threadIdx.x + o]);
+      smx[threadIdx.x] = fmaxf(smx[threadIdx.x], smx[threadIdx.x + o]);
+      ssl[threadIdx.x] += ssl[threadIdx.x + o];
+      ssh[threadIdx.x] += ssh[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double* o = part + 4 * static_cast<size_t>(blockIdx.x);
+    o[0] = smn[0];
+    o[1] = smx[0];
+    o[2] = ssl[0];
+    o[3] = ssh[0];
+  }
+}
+
+__device__ void oc_make_candidates(double* oc) {
+  const double lo = oc[OC_SLO], hi = oc[OC_SHI];
+  const double lr = log(hi / lo);
+  for (int k = 0; k < kOcCand; ++k) oc[OC_CAND + k] = lo * exp(lr * (k + 1) / (kOcCand + 1));
+}
+
+__global__ void k_oc_setup_final(const double* __restrict__ part, int nblk, size_t N, double V,
+                                 double* __restrict__ oc) {
+  if (threadIdx.x != 0) return;
+  double mn = INFINITY, mx = 0.0, sl = 0.0, sh = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    mn = fmin(mn, part[4 * b]);
+    mx = fmax(mx, part[4 * b + 1]);
+    sl += part[4 * b + 2];
+    sh += part[4 * b + 3];
+  }
+  const double vlo = sl / static_cast<double>(N), vhi = sh / static_cast<double>(N);
+  oc[OC_SLO] = mn;
+  oc[OC_SHI] = mx;
+  if (!(mx > 0.0) || !isfinite(mn) || vlo >= V) oc[OC_MODE] = 2;     // everything at its lower bound
+  else if (vhi <= V) oc[OC_MODE] = 1;                                // everything at its upper bound
+  else oc[OC_MODE] = 0;
+  if (oc[OC_MODE] == 0) oc_make_candidates(oc);
+}
+
+__global__ void __launch_bounds__(256) k_oc_pass(const float* __restrict__ rho,
+                                                 const float* __restrict__ base, size_t N,
+                                                 float move, float rmin,
+                                                 const double* __restrict__ oc,
+                                                 double* __restrict__ part) {
+  if (oc[OC_MODE] != 0) return;
+  float cand[kOcCand], acc[kOcCand];
+  double accd[kOcCand];
+#pragma unroll
+  for (int k = 0; k < kOcCand; ++k) {
+    cand[k] = static_cast<float>(oc[OC_CAND + k]);
+    acc[k] = 0.f;
+    accd[k] = 0.0;
+  }
+  int cnt = 0;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const float r = __ldg(rho + e), bs = __ldg(base + e);
+    const float lo = oc_lo(r, move, rmin), hi = oc_hi(r, move);
+#pragma unroll
+    for (int k = 0; k < kOcCand; ++k) acc[k] += fminf(fmaxf(bs * cand[k], lo), hi);
+    if (++cnt == 8) {   // FP32 over at most 8 terms, FP64 beyond
+#pragma unroll
+      for (int k = 0; k < kOcCand; ++k) {
+        accd[k] += acc[k];
+        acc[k] = 0.f;
+      }
+      cnt = 0;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kOcCand; ++k) accd[k] += acc[k];
+  block_sum_store_d<kOcCand>(accd, part);
+}
+
+// sums: the kOcCand volume sums already reduced over blocks.
+__global__ void k_oc_pass_final(const double* __restrict__ sums, size_t N, double V,
+                                double* __restrict__ oc) {
+  if (threadIdx.x != 0 || oc[OC_MODE] != 0) return;
+  double lo = oc[OC_SLO], hi = oc[OC_SHI];
+  for (int k = 0; k < kOcCand; ++k) {
+    const double vol = sums[k] / static_cast<double>(N);
+    if (vol <= V) {
+      lo = oc[OC_CAND + k];
+    } else {
+      hi = oc[OC_CAND + k];
+      break;
+    }
+  }
+  oc[OC_SLO] = lo;
+  oc[OC_SHI] = hi;
+  oc_make_candidates(oc);
+}
+
+__global__ void __launch_bounds__(256) k_oc_apply(float* __restrict__ rho,
+                                                  const float* __restrict__ base, size_t N,
+                                                  float move, float rmin,
+                                                  const double* __restrict__ oc,
+                                                  double* __restrict__ part) {
+  const int mode = static_cast<int>(oc[OC_MODE]);
+  const float s = mode == 2 ? 0.f : static_cast<float>(mode == 1 ? oc[OC_SHI] : oc[OC_SLO]);
+  float ch = 0.f;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const float r = rho[e];
+    const float lo = oc_lo(r, move, rmin), hi = oc_hi(r, move);
+    const float nr = fminf(fmaxf(base[e] * s, lo), hi);
+    ch = fmaxf(ch, fabsf(nr - r));
+    rho[e] = nr;
+  }
+  __shared__ float sm[256];
+  sm[threadIdx.x] = ch;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+
+__global__ void k_max_partials(const double* __restrict__ part, int nblk, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double m = 0.0;
+  for (int b = 0; b < nblk; ++b) m = fmax(m, part[b]);
+  *out = m;
+}
+
+}  // namespace
+
+int reduce_grid(size_t n_items) { return grid_for(n_items, 256); }
+
+cudaError_t launch_sum_partials(const double* part, int nblk, int nv, double* out,
+                                cudaStream_t s) {
+  k_sum_partials<<<1, 256, 0, s>>>(part, nblk, nv, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot6(const float* a, const float* b, size_t N, double* part, int* grid_out,
+                        cudaStream_t s) {
+  const int g = grid_for(N, 256);
+  *grid_out = g;
+  k_dot6<<<g, 256, 0, s>>>(a, b, N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot6_zsum(const float* r, const float* z, size_t N, double* part,
+                             int* grid_out, cudaStream_t s) {
+  const int g = grid_for(N, 256);
+  *grid_out = g;
+  k_dot6_zsum<<<g, 256, 0, s>>>(r, z, N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_alpha(double* scal, cudaStream_t s) {
+  k_cg_alpha<<<1, 32, 0, s>>>(scal);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_beta(double* scal, int first, cudaStream_t s) {
+  k_cg_beta<<<1, 32, 0, s>>>(scal, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_active(double* scal, double tol, int centre, size_t N, cudaStream_t s) {
+  k_cg_active<<<1, 32, 0, s>>>(scal, tol * tol, centre, static_cast<double>(N));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_center(float* r, const double* scal, size_t N, cudaStream_t s) {
+  k_center<<<grid_for(N, 256), 256, 0, s>>>(r, scal, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update_xr(float* u, float* ulo, float* r, const float* p, const float* q,
+                                const double* scal, size_t N, double* part, int* grid_out,
+                                cudaStream_t s) {
+  const int g = grid_for(N, 256);
+  *grid_out = g;
+  k_cg_update_xr<<<g, 256, 0, s>>>(u, ulo, r, p, q, scal, N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update_p(float* p, const float* z, const double* scal, size_t N,
+                               cudaStream_t s) {
+  k_cg_update_p<<<grid_for(N, 256), 256, 0, s>>>(p, z, scal, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_set(float* hi, float* lo, const float* src, size_t n, cudaStream_t s) {
+  k_split_set<<<grid_for(n, 256), 256, 0, s>>>(hi, lo, src, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_get(const float* hi, const float* lo, float* dst, size_t n,
+                             cudaStream_t s) {
+  k_split_get<<<grid_for(n, 256), 256, 0, s>>>(hi, lo, dst, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_filter(const FilterParam& fp, int n, const float* in, float* out,
+                          cudaStream_t s) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  k_filter<<<grid_for(N, 256), 256, 0, s>>>(fp, n, in, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oc(homo_ctx* c, const float* dc, float* rho, double volfrac, double move,
+                      double eta, double rho_min, double* change) {
+  const size_t N = c->N;
+  const int g = grid_for(N, 256);
+  double* oc = c->scal + S_OC;
+  cudaStream_t s = c->stream;
+  k_oc_setup<<<g, 256, 0, s>>>(rho, dc, c->tmp, N, static_cast<float>(eta), static_cast<float>(move),
+                               static_cast<float>(rho_min), c->part);
+  k_oc_setup_final<<<1, 32, 0, s>>>(c->part, g, N, volfrac, oc);
+  for (int it = 0; it < kOcPasses; ++it) {
+    k_oc_pass<<<g, 256, 0, s>>>(rho, c->tmp, N, static_cast<float>(move), static_cast<float>(rho_min), oc,
+                                c->part);
+    k_sum_partials<<<1, 256, 0, s>>>(c->part, g, kOcCand, oc + OC_SUMS);
+    k_oc_pass_final<<<1, 32, 0, s>>>(oc + OC_SUMS, N, volfrac, oc);
+  }
+  k_oc_apply<<<g, 256, 0, s>>>(rho, c->tmp, N, static_cast<float>(move), static_cast<float>(rho_min), oc,
+                               c->part);
+  k_max_partials<<<1, 32, 0, s>>>(c->part, g, oc + OC_CHANGE);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (change) {
+    e = cudaMemcpyAsync(c->hscal + S_OC + OC_CHANGE, oc + OC_CHANGE, sizeof(double),
+                        cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    *change = c->hscal[S_OC + OC_CHANGE];
+  }
+  return cudaSuccess;
+}
+
+}  // namespace homo

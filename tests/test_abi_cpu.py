@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every symbol include/homo.h declares (CPU only).
+
+Only host-arithmetic entry points are called here (element matrix, objectives, argument
+validation that returns before any CUDA call); nothing launches a kernel.
+"""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2301_08911_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "homo.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(homo_[a-z_A-Z0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(binding.LIB_PATH):
+        from paper_2301_08911_gb300 import build
+        build.build()
+    return binding.load_library()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for must in ("homo_create", "homo_destroy", "homo_set_density", "homo_solve_cases", "homo_CH",
+                 "homo_sensitivity", "homo_filter", "homo_update"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    for name in names:
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (homo_\w+)", out))
+    assert set(names) <= exported
+    assert set(binding.SIGNATURES) == set(names)
+
+
+def test_element_matrix_matches_oracle_quadrature(lib):
+    for nu in (0.3, 0.2, 0.45):
+        K = binding.element_matrix(nu)
+        Ko = oracle.ke_hex8(1.0, nu, 1.0)
+        assert np.abs(K - Ko).max() < 4e-7 * np.abs(Ko).max()
+
+
+@pytest.mark.parametrize("kind", ["bulk", "shear", "poisson", "logpoisson"])
+def test_objectives_match_oracle(lib, kind):
+    rng = np.random.default_rng(3)
+    C = oracle.elasticity_matrix(1.0, 0.3) + 0.01 * rng.standard_normal((6, 6))
+    C = 0.5 * (C + C.T)
+    f, g = binding.objective(kind, C, 4, 0.8 if kind == "poisson" else 1.0)
+    fo, go = oracle.objective(kind, C, 4)
+    assert abs(f - fo) < 1e-14
+    S = rng.standard_normal((6, 6))
+    S = S + S.T            # symmetric directions: the two gradient conventions agree there
+    assert abs(np.sum(g * S) - np.sum(go * S)) < 1e-13
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    h = ctypes.c_void_p()
+    for args in ((3, 1.0, 0.3, 3.0, 1e-9), (16, 1.0, 0.5, 3.0, 1e-9), (16, -1.0, 0.3, 3.0, 1e-9),
+                 (16, 1.0, 0.3, 0.5, 1e-9), (16, 1.0, 0.3, 3.0, 2.0), (18, 1.0, 0.3, 3.0, 1e-9)):
+        st = lib.homo_create(ctypes.byref(h), *args, None)
+        assert st == binding.HOMO_EINVAL, args
+        assert lib.homo_last_error(None)
+    assert lib.homo_destroy(None) == binding.HOMO_OK
+    assert lib.homo_status_string(binding.HOMO_ENOCONV).decode().startswith("not converged")

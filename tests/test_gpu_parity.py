@@ -1,0 +1,358 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, on a GB300.
+
+Units: the library works in voxel units (element side 1), the oracle in the paper's
+Omega = [0,1]^3 with h = 1/n. Conversions used below: K_voxel = K_h / h,
+f_voxel = f_h / h^2, u_voxel = u_h / h; C^H and sensitivities need none.
+Tolerances (FP32 storage/arithmetic, FP64 reductions): C^H and sensitivities relative
+1e-6 (Frobenius / L2), operators relative 2e-6 in L2 of the output.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from synthetic import (laminate_density, smoothed_threshold_density, uniform_density,
+                       uniform_field)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2301_08911_gb300 import binding, build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    return binding
+
+
+def cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def planes(v6, n):
+    """oracle (6, 3N) with dof 3v+comp -> library planes (18, N)."""
+    return np.asarray(v6).reshape(6, n ** 3, 3).transpose(0, 2, 1).reshape(18, n ** 3)
+
+
+def dofs(p18, n):
+    """library planes (18, N) -> oracle (6, 3N)."""
+    return np.asarray(p18).reshape(6, 3, n ** 3).transpose(0, 2, 1).reshape(6, 3 * n ** 3)
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def mean_free(v18):
+    return v18 - v18.mean(axis=1, keepdims=True)
+
+
+def make(B, n, **kw):
+    return B.Homogenization(n, **kw)
+
+
+# ---------------------------------------------------------------- operators
+@pytest.mark.parametrize("n", [16, 20, 24])
+def test_loads_match_oracle(B, n):
+    rho = uniform_density(n, 100 + n)
+    hom = make(B, n)
+    hom.set_density(cuda(rho))
+    f = torch.empty(18 * n ** 3, device="cuda")
+    hom.get_loads(f)
+    h = 1.0 / n
+    E = oracle.simp_modulus(rho)
+    ref = planes(oracle.macro_strain_loads(n, E, oracle.ke_hex8(1, 0.3, h), oracle.macro_strain_displacements(h)), n) / h ** 2
+    assert rel(host(f).reshape(18, -1), ref) < 2e-6
+
+
+@pytest.mark.parametrize("n", [16, 20])
+def test_apply_K_matches_oracle(B, n):
+    rho = uniform_density(n, 200 + n, 0.001, 1.0)
+    u = uniform_field(18 * n ** 3, 201, -1, 1)
+    hom = make(B, n)
+    hom.set_density(cuda(rho))
+    out = torch.empty(18 * n ** 3, device="cuda")
+    hom.apply_K(cuda(u), out)
+    h = 1.0 / n
+    K = oracle.assemble_K(n, oracle.simp_modulus(rho), oracle.ke_hex8(1, 0.3, h))
+    ref = planes((K @ dofs(u.reshape(18, -1).astype(np.float64), n).T).T, n) / h
+    assert rel(host(out).reshape(18, -1), ref) < 2e-6
+
+
+def test_galerkin_stencils_match_oracle(B):
+    n = 16
+    rho = uniform_density(n, 300, 0.001, 1.0)
+    hom = make(B, n)
+    assert hom.num_levels == 3 and [hom.level_size(l) for l in range(3)] == [16, 8, 4]
+    hom.set_density(cuda(rho))
+    h = 1.0 / n
+    K = oracle.assemble_K(n, oracle.simp_modulus(rho), oracle.ke_hex8(1, 0.3, h)) / h
+    mats = [K]
+    for l in (1, 2):
+        mats.append(oracle.galerkin(mats[-1], n >> l))
+    for l in (0, 1, 2):
+        nl = n >> l
+        st = torch.empty(243 * nl ** 3, device="cuda")
+        hom.get_stencil(l, st)
+        ref = oracle.vertex_stencil(mats[l], nl)
+        assert rel(host(st).reshape(nl ** 3, 27, 3, 3), ref) < 2e-6, l
+
+
+def test_restrict_and_prolong_match_oracle(B):
+    n = 16
+    hom = make(B, n)
+    P = oracle.prolongation(n // 2)
+    r = uniform_field(18 * n ** 3, 400, -1, 1).reshape(18, -1)
+    c = torch.empty(18 * (n // 2) ** 3, device="cuda")
+    hom.restrict(0, cuda(r), c)
+    ref = planes((P.T @ dofs(r.astype(np.float64), n).T).T, n // 2)
+    assert rel(host(c).reshape(18, -1), ref) < 1e-6
+    xc = uniform_field(18 * (n // 2) ** 3, 401, -1, 1).reshape(18, -1)
+    xf = torch.empty(18 * n ** 3, device="cuda")
+    hom.prolong(0, cuda(xc), xf)
+    ref = planes((P @ dofs(xc.astype(np.float64), n // 2).T).T, n)
+    assert rel(host(xf).reshape(18, -1), ref) < 1e-6
+
+
+@pytest.mark.parametrize("level,reverse", [(0, False), (0, True), (1, False)])
+def test_gauss_seidel_sweep_matches_oracle(B, level, reverse):
+    n = 8
+    rho = uniform_density(n, 500, 0.05, 1.0)
+    hom = make(B, n, min_coarse=3)      # levels 8, 4
+    hom.set_density(cuda(rho))
+    h = 1.0 / n
+    K = oracle.assemble_K(n, oracle.simp_modulus(rho), oracle.ke_hex8(1, 0.3, h)) / h
+    if level == 1:
+        K = oracle.galerkin(K, n // 2)
+    nl = n >> level
+    f = mean_free(uniform_field(18 * nl ** 3, 501, -1, 1).reshape(18, -1).astype(np.float64))
+    u0 = uniform_field(18 * nl ** 3, 502, -1, 1).reshape(18, -1).astype(np.float64)
+    ut = cuda(u0)
+    hom.smooth(level, reverse, cuda(f), ut)
+    order = list(range(8))[::-1] if reverse else list(range(8))
+    fd, ud = dofs(f, nl), dofs(u0, nl)
+    ref = np.stack([oracle.gs_sweep(K, nl, ud[i], fd[i], order) for i in range(6)])
+    assert rel(dofs(host(ut).reshape(18, -1), nl), ref) < 2e-6
+
+
+def test_vcycle_is_symmetric_positive(B):
+    n = 16
+    hom = make(B, n)
+    hom.set_density(cuda(smoothed_threshold_density(n, 0.3, 1)))
+    x = mean_free(uniform_field(18 * n ** 3, 600, -1, 1).reshape(18, -1).astype(np.float64))
+    y = mean_free(uniform_field(18 * n ** 3, 601, -1, 1).reshape(18, -1).astype(np.float64))
+    zx, zy = torch.empty(18 * n ** 3, device="cuda"), torch.empty(18 * n ** 3, device="cuda")
+    hom.vcycle(cuda(x), zx)
+    hom.vcycle(cuda(y), zy)
+    Mx, My = host(zx).reshape(18, -1), host(zy).reshape(18, -1)
+    for c in range(6):
+        s = slice(3 * c, 3 * c + 3)
+        a, b = np.sum(y[s] * Mx[s]), np.sum(x[s] * My[s])
+        assert abs(a - b) <= 1e-5 * np.sqrt(np.sum(x[s] * Mx[s]) * np.sum(y[s] * My[s]))
+        assert np.sum(x[s] * Mx[s]) > 0
+
+
+# ---------------------------------------------------------------- solve, C^H, sensitivity
+_CASES = {}
+
+
+def _solved(B, n, kind):
+    key = (n, kind)
+    if key in _CASES:
+        return _CASES[key]
+    if kind == "c1":
+        rho = smoothed_threshold_density(n, 0.3, 1)
+    else:
+        rho = uniform_density(n, 700 + n, 0.05, 1.0)
+    rho_t = oracle.cone_filter(rho, n, 2.0).astype(np.float32)
+    ref = oracle.homogenize(rho_t.astype(np.float64), n)
+    hom = make(B, n)
+    hom.set_density(cuda(rho_t))
+    # well below the configs' 1e-6 so that the comparison measures the kernels' FP32
+    # arithmetic, not the stopping tolerance (the sensitivity error is first order in it)
+    its, relres, _ = hom.solve_cases(1e-9, 600, warm_start=False)
+    _CASES[key] = (hom, rho_t, ref, its, relres)
+    return _CASES[key]
+
+
+@pytest.mark.parametrize("n,kind", [(16, "c1"), (20, "uniform"), (24, "uniform"), (12, "uniform")])
+def test_CH_matches_oracle(B, n, kind):
+    hom, rho_t, ref, its, relres = _solved(B, n, kind)
+    assert max(relres) <= 1e-9
+    assert hom.residual_history().shape[1] == 6
+    C = hom.CH()
+    assert np.abs(C - C.T).max() == 0.0
+    assert rel(C, ref["C"]) < 1e-6, (C, ref["C"])
+
+
+@pytest.mark.parametrize("n,kind", [(16, "c1"), (20, "uniform")])
+def test_sensitivity_matches_oracle(B, n, kind):
+    hom, rho_t, ref, _, _ = _solved(B, n, kind)
+    for objective in ("bulk", "shear"):
+        _, g = oracle.objective(objective, ref["C"])
+        s = torch.empty(n ** 3, device="cuda")
+        hom.sensitivity(g, s)
+        sref = oracle.sensitivity(rho_t.astype(np.float64), ref["q"], g)
+        assert rel(host(s), sref) < 1e-6
+
+
+def test_displacements_match_oracle_in_energy_norm(B):
+    """At 5e8 stiffness contrast the void displacements are weakly determined by the
+    residual, so the fields are compared in the energy norm: for the error e of case i,
+    e^T K e equals the error of C^H_ii (K (chi - u) = 0 at the exact solution)."""
+    n = 16
+    hom, rho_t, ref, _, _ = _solved(B, n, "c1")
+    u = torch.empty(18 * n ** 3, device="cuda")
+    hom.get_displacement(u)
+    got = dofs(host(u).reshape(18, -1), n) / n            # u_h = h * u_voxel
+    for i in range(6):
+        e = got[i] - ref["u"][i]
+        assert e @ (ref["K"] @ e) <= 1e-6 * ref["C"][i, i]
+
+
+@pytest.mark.parametrize("n", [4, 5, 6])
+def test_single_level_direct_solve(B, n):
+    rho_t = uniform_density(n, 800 + n, 0.1, 1.0)
+    ref = oracle.homogenize(rho_t.astype(np.float64), n)
+    hom = make(B, n)
+    assert hom.num_levels == 1
+    hom.set_density(cuda(rho_t))
+    _, relres, _ = hom.solve_cases(1e-7, 50, warm_start=False)
+    assert rel(hom.CH(), ref["C"]) < 1e-6
+
+
+# ---------------------------------------------------------------- closed forms on the GPU
+@pytest.mark.parametrize("n", [16, 32])
+def test_full_solid_is_isotropic_D(B, n):
+    hom = make(B, n)
+    hom.set_density(cuda(np.ones(n ** 3)))
+    its, relres, _ = hom.solve_cases(1e-6, 50, warm_start=False)
+    assert its == [0] * 6
+    D = oracle.elasticity_matrix(1.0, 0.3)
+    assert np.abs(hom.CH() - D).max() < 1e-6
+
+
+@pytest.mark.parametrize("n,axis", [(32, 0), (32, 2), (64, 1)])
+def test_laminate_matches_backus(B, n, axis):
+    vals = np.array([1.0, 0.1, 0.5, 0.1]) ** (1 / 3)
+    rho = laminate_density(n, axis, vals)
+    hom = make(B, n, Emin=0.0)
+    hom.set_density(cuda(rho))
+    hom.solve_cases(1e-7, 300, warm_start=False)
+    E = oracle.simp_modulus(rho, Emin=0.0)
+    nu = 0.3
+    M = E * (1 - nu) / ((1 + nu) * (1 - 2 * nu))
+    G = E / (2 * (1 + nu))
+    r = nu / (1 - nu)
+    C = np.zeros((6, 6))
+    C00 = 1 / np.mean(1 / M)
+    C[0, 0] = C00
+    C[0, 1] = C[1, 0] = C[0, 2] = C[2, 0] = r * C00
+    C[1, 1] = C[2, 2] = np.mean(E) / (1 - nu ** 2) + r * r * C00
+    C[1, 2] = C[2, 1] = nu * np.mean(E) / (1 - nu ** 2) + r * r * C00
+    C[3, 3] = C[5, 5] = 1 / np.mean(1 / G)
+    C[4, 4] = np.mean(G)
+    P = [[0, 1, 2, 3, 4, 5], [1, 0, 2, 3, 5, 4], [2, 1, 0, 4, 3, 5]][axis]
+    assert rel(hom.CH(), C[np.ix_(P, P)]) < 1e-6
+
+
+# ---------------------------------------------------------------- filter and OC
+@pytest.mark.parametrize("n,radius", [(16, 2.0), (20, 1.5), (12, 3.0)])
+def test_filter_matches_oracle(B, n, radius):
+    x = uniform_density(n, 900 + n, 0.0, 1.0)
+    hom = make(B, n)
+    out = torch.empty(n ** 3, device="cuda")
+    hom.filter(radius, cuda(x), out)
+    assert rel(host(out), oracle.cone_filter(x.astype(np.float64), n, radius)) < 1e-6
+
+
+@pytest.mark.parametrize("n,t", [(16, 0.3), (20, 0.7)])
+def test_oc_update_matches_oracle(B, n, t):
+    rho = uniform_density(n, 1000 + n, 0.001, 1.0)
+    dc = -uniform_density(n, 1001 + n, 0.0, 1.0) ** 3 * 1e-5
+    lo = np.maximum(1e-3, rho - 0.05).mean()
+    hi = np.minimum(1.0, rho + 0.05).mean()
+    V = float(lo + t * (hi - lo))          # attainable volume inside the move limits
+    hom = make(B, n)
+    r = cuda(rho)
+    change = hom.update(cuda(dc), r, V, 0.05, 0.5, 1e-3)
+    new_ref, _, ch_ref = oracle.oc_update(rho.astype(np.float64), dc.astype(np.float64), V)
+    got = host(r)
+    assert np.abs(got - new_ref).max() < 2e-6
+    assert abs(got.mean() - V) < 1e-6
+    assert abs(change - ch_ref) < 2e-6
+
+
+def test_oc_unattainable_volume_goes_to_bounds(B):
+    n = 8
+    rho = uniform_density(n, 1100, 0.5, 0.9)
+    dc = -uniform_density(n, 1101, 0.1, 1.0)
+    hom = make(B, n)
+    r = cuda(rho)
+    hom.update(cuda(dc), r, 0.05, 0.05, 0.5, 1e-3)       # below every lower bound
+    assert np.allclose(host(r), np.maximum(1e-3, rho - 0.05), atol=1e-7)
+    r = cuda(rho)
+    hom.update(cuda(dc), r, 0.99, 0.05, 0.5, 1e-3)       # above every upper bound
+    assert np.allclose(host(r), np.minimum(1.0, rho + 0.05), atol=1e-7)
+
+
+# ---------------------------------------------------------------- whole iteration
+def test_full_iteration_matches_oracle_16(B):
+    """One bulk-modulus iteration at 16^3 on the blurred-noise cell at volume fraction 0.3."""
+    n, V = 16, 0.3
+    rho = smoothed_threshold_density(n, V, 1)
+    ref = oracle.optimization_iteration(rho.astype(np.float64), n, V, "bulk")
+    hom = make(B, n)
+    r = cuda(rho)
+    rt = torch.empty_like(r)
+    hom.filter(2.0, r, rt)
+    hom.set_density(rt)
+    hom.solve_cases(1e-6, 300, warm_start=False)
+    C = hom.CH()
+    f, g = B.objective("bulk", C)
+    s = torch.empty_like(r)
+    hom.sensitivity(g, s)
+    dc = torch.empty_like(r)
+    hom.filter(2.0, s, dc)
+    change = hom.update(dc, r, V, 0.05, 0.5, 1e-3)
+    assert rel(C, ref["C"]) < 1e-6
+    assert abs(f - ref["f_obj"]) < 1e-6 * abs(ref["f_obj"])
+    assert rel(host(dc), ref["dc"]) < 1e-5
+    assert np.abs(host(r) - ref["rho_new"]).max() < 1e-5
+    assert abs(change - ref["change"]) < 1e-5
+
+
+def test_warm_start_reuses_fields(B):
+    n = 16
+    hom = make(B, n)
+    hom.set_density(cuda(smoothed_threshold_density(n, 0.3, 1)))
+    its0, _, _ = hom.solve_cases(1e-6, 300, warm_start=False)
+    its1, _, _ = hom.solve_cases(1e-6, 300, warm_start=True)
+    assert max(its1) == 0 and max(its0) > 0
+
+
+# ---------------------------------------------------------------- errors
+def test_errors_are_status_codes(B):
+    n = 8
+    hom = make(B, n)
+    with pytest.raises(B.HomoError) as e:
+        hom.solve_cases(1e-6)
+    assert e.value.status == B.HOMO_ESTATE
+    with pytest.raises(B.HomoError) as e:
+        hom.CH()
+    assert e.value.status == B.HOMO_ESTATE
+    x = torch.zeros(n ** 3, device="cuda")
+    with pytest.raises(B.HomoError) as e:
+        hom.filter(5.0, x, torch.empty_like(x))
+    assert e.value.status == B.HOMO_EINVAL
+    with pytest.raises(B.HomoError):
+        hom.filter(2.0, x, x)
+    hom.set_density(cuda(uniform_density(n, 1200)))
+    _, _, st = hom.solve_cases(1e-12, 1, warm_start=False, raise_on_noconv=False)
+    assert st == B.HOMO_ENOCONV

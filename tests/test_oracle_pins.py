@@ -104,6 +104,17 @@ def test_loads_vanish_for_uniform_density_and_sum_to_zero():
     assert np.abs(f).max() > 1e-3
 
 
+def test_vertex_form_loads_match_assembled_loads():
+    """Eq. 11 per vertex equals the element-by-element assembly of Eq. 4."""
+    n = 5
+    h = 1 / n
+    E = oracle.simp_modulus(uniform_density(n, 15))
+    Ke, chi = oracle.ke_hex8(1, 0.3, h), oracle.macro_strain_displacements(h)
+    f = oracle.macro_strain_loads(n, E, Ke, chi)
+    got = oracle.macro_strain_loads_at_vertices(n, E, Ke, chi, np.arange(n ** 3))
+    assert np.allclose(got.reshape(6, -1), f, rtol=0, atol=1e-15)
+
+
 def test_loads_equal_K_times_global_linear_field_in_the_interior():
     """f^i = K chi^i(global coords) on vertices whose incident elements do not wrap."""
     n = 4
