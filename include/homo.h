@@ -138,6 +138,31 @@ int homo_set_density(homo_ctx* ctx, const float* rho, int on_device);
 int homo_solve_cases(homo_ctx* ctx, double rel_tol, int max_iters, int warm_start,
                      int iters_out[6], double relres_out[6]);
 
+/* C^H without any device allocation (the paper has no counterpart to this entry point).
+ * For callers that cannot call cudaMalloc while they run: an application that sets its
+ * device-memory budget once at start-up, a framework whose own pooled allocator must
+ * own every device byte, or a process whose device memory is already fully reserved.
+ * Such callers hold the fields themselves and need no context (homo_create allocates).
+ * Computes the same C^H as homo_CH (Eq. 7) from caller-owned buffers:
+ *   n     : cells per axis, 4 <= n <= 1024 (larger n returns HOMO_EINVAL with a message
+ *           in homo_last_error(NULL));
+ *   nu    : Poisson's ratio of the unit-modulus element matrix;
+ *   E     : device, N floats, element moduli E_e (as homo_set_density derives them);
+ *   u, ulo: device, 18*N floats each (6-case layout above): displacement, optionally
+ *           split into high and low parts; ulo may be NULL (treated as zero);
+ *   CH    : host, 36 doubles, row-major 6x6 (output);
+ *   cuda_stream: the stream to run on (NULL = legacy default stream).
+ * Scratch: instead of allocating, the call uses one fixed array of about 200 KB that
+ * every GPU which loads the library holds until the process exits. Its size does not
+ * grow with n. The first call on a device, with that device current, looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before any stream
+ * capture. All calls share the array and it keeps the last call's contents (each call
+ * overwrites every entry it later reads, so nothing needs clearing); calls that overlap
+ * on the GPU, on any stream, race and must be serialised by the caller. Synchronises
+ * the stream. Calls no cudaMalloc, cudaFree or allocating library routine. */
+int homo_CH_noalloc(int n, double nu, const float* E, const float* u, const float* ulo,
+                    double CH[36], void* cuda_stream);
+
 /* Homogenised tensor C^H_ij = (1/|Omega|) sum_e E_e (chi_i - u_i)_e^T K0 (chi_j - u_j)_e
  * (Eq. 7) from the last solve. CH: host, 36 doubles, row-major 6x6, Voigt order
  * 11,22,33,12,23,13, engineering shear. Synchronises the stream. */

@@ -64,6 +64,7 @@ SIGNATURES = {
     "homo_kernel_class_name": (ctypes.c_char_p, [ctypes.c_int]),
     "homo_launch_count": (ctypes.c_longlong, [_vp]),
     "homo_residual_history": (ctypes.c_int, [_vp, _c_double_p, ctypes.c_int]),
+    "homo_CH_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _c_double_p, _vp]),
 }
 
 KERNEL_CLASSES = 13

@@ -223,6 +223,11 @@ int precondition_and_direction(homo_ctx* c, int first) {
 
 }  // namespace
 
+namespace homo {
+// Message returned by homo_last_error(NULL) on this thread (context-free entry points).
+void set_thread_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace homo
+
 extern "C" {
 
 int homo_version(void) { return 100; }

@@ -7,6 +7,9 @@
 // and its neighbour v + d is
 //     A_d = sum over (t, j) with bits(t) + bits(j) - 1 = d of E_t * K0[7 - t, j],
 // built once per vertex and applied to all 6 load cases (the 6 cases share E and K0).
+#include <mutex>
+#include <string>
+
 #include "dev_common.cuh"
 
 namespace homo {
@@ -490,4 +493,160 @@ cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, flo
   return cudaGetLastError();
 }
 
+void set_thread_error(const std::string& msg);
+
+// ---------------------------------------------------------------- allocation-free C^H
+// A second way to evaluate C^H for callers that cannot allocate device memory while
+// they run. Its per-block partial sums go to one fixed array in device memory that the
+// library reserves when it is loaded, instead of to context buffers from cudaMalloc.
+namespace {
+
+constexpr int kNoAllocBlocks = 1216;   // partial-sum rows: 152 SMs x 8 blocks
+constexpr int kNoAllocMaxN = 1024;     // largest cell per axis (indices stay in int)
+
+// Rows 0..kNoAllocBlocks-1: 21 partial sums per block; last row: the 21 totals.
+// Every GPU that loads the library holds this array (about 200 KB) until exit.
+static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocBlocks + 1) * 21];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch, per device
+
+// Same element arithmetic as the C^H mode of k_fine_elem; ulo may be null (read as 0).
+__global__ void __launch_bounds__(kElemBlock) k_ch_noalloc(const __grid_constant__ KeParam K,
+                                                           const __grid_constant__ ChiParam X,
+                                                           const float* __restrict__ E,
+                                                           const float* __restrict__ u,
+                                                           const float* __restrict__ ulo, int n,
+                                                           double* __restrict__ scratch) {
+  extern __shared__ float wsh[];
+  float* w = wsh + threadIdx.x * kElemStride;
+  const size_t N = static_cast<size_t>(n) * n * n;
+  float cs[21], cc[21];
+#pragma unroll
+  for (int k = 0; k < 21; ++k) cs[k] = cc[k] = 0.f;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(e % n), y = static_cast<int>((e / n) % n),
+              z = static_cast<int>(e / (static_cast<size_t>(n) * n));
+    const int xs[2] = {x, x == n - 1 ? 0 : x + 1};
+    const int ys[2] = {y * n, (y == n - 1 ? 0 : y + 1) * n};
+    const int zs[2] = {z * n * n, (z == n - 1 ? 0 : z + 1) * n * n};
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) {
+      const float* uq = u + static_cast<size_t>(q) * N;
+      const float* lq = ulo ? ulo + static_cast<size_t>(q) * N : nullptr;
+      const float h0 = __ldg(uq + e), l0 = lq ? __ldg(lq + e) : 0.f;
+      const int c = q / 3, k = q % 3;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t vj = static_cast<size_t>(xs[j & 1] + ys[(j >> 1) & 1] + zs[j >> 2]);
+        const float du = (__ldg(uq + vj) - h0) + (lq ? (__ldg(lq + vj) - l0) : 0.f);
+        w[c * 24 + 3 * j + k] = X.chi[c][3 * j + k] - du;
+      }
+    }
+    float* q = w + 144;
+#pragma unroll 1
+    for (int i = 0, idx = 0; i < kCases; ++i) {
+      float yv[24];
+#pragma unroll
+      for (int r = 0; r < 24; ++r) yv[r] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 24; ++k) {
+        const float wk = w[i * 24 + k];
+#pragma unroll
+        for (int r = 0; r < 24; ++r) yv[r] = fmaf(K.k[r * 24 + k], wk, yv[r]);
+      }
+#pragma unroll 1
+      for (int j = i; j < kCases; ++j, ++idx) {
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < 24; ++k) s = fmaf(yv[k], w[j * 24 + k], s);
+        q[idx] = s;
+      }
+    }
+    const float Ee = __ldg(E + e);
+#pragma unroll
+    for (int k = 0; k < 21; ++k) {
+      const float yk = fmaf(Ee, q[k], -cc[k]);
+      const float t = cs[k] + yk;
+      cc[k] = (t - cs[k]) - yk;
+      cs[k] = t;
+    }
+  }
+  block_sum_store<21>(cs, scratch);
+}
+
+// totals[k] = sum over the nblk rows written by this call, fixed order.
+__global__ void k_ch_noalloc_total(double* __restrict__ scratch, int nblk) {
+  const int k = threadIdx.x;
+  if (k >= 21) return;
+  double s = 0.0;
+  for (int b = 0; b < nblk; ++b) s += scratch[static_cast<size_t>(b) * 21 + k];
+  scratch[static_cast<size_t>(kNoAllocBlocks) * 21 + k] = s;
+}
+
+int noalloc_fail(int code, const std::string& msg) {
+  set_thread_error(msg);
+  return code;
+}
+
+}  // namespace
+
 }  // namespace homo
+
+extern "C" int homo_CH_noalloc(int n, double nu, const float* E, const float* u, const float* ulo,
+                               double CH[36], void* cuda_stream) {
+  using namespace homo;
+  if (n < 4 || n > kNoAllocMaxN)
+    return noalloc_fail(HOMO_EINVAL, "homo_CH_noalloc: n = " + std::to_string(n) +
+                                         " is outside [4, " + std::to_string(kNoAllocMaxN) +
+                                         "], the largest cell its fixed scratch array serves");
+  if (!(nu > -1.0 && nu < 0.5) || !E || !u || !CH)
+    return noalloc_fail(HOMO_EINVAL, "homo_CH_noalloc: bad nu or null pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= 256)
+    return noalloc_fail(HOMO_ECUDA, std::string("homo_CH_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p)
+        return noalloc_fail(HOMO_ECUDA, std::string("homo_CH_noalloc: cudaGetSymbolAddress: ") +
+                                            cudaGetErrorString(e));
+      g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    scratch = g_noalloc_ptr[dev];
+  }
+  KeParam ke;
+  LoadParam ld;
+  ChiParam chi;
+  build_element_matrix(nu, ke, ld, chi);
+  const size_t N = static_cast<size_t>(n) * n * n;
+  size_t blocks = (N + kElemBlock - 1) / kElemBlock;
+  if (blocks > static_cast<size_t>(kNoAllocBlocks)) blocks = kNoAllocBlocks;
+  const size_t shm = static_cast<size_t>(kElemBlock) * kElemStride * sizeof(float);
+  e = cudaFuncSetAttribute(k_ch_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm));
+  if (e == cudaSuccess) {
+    k_ch_noalloc<<<static_cast<int>(blocks), kElemBlock, shm, s>>>(ke, chi, E, u, ulo, n, scratch);
+    k_ch_noalloc_total<<<1, 32, 0, s>>>(scratch, static_cast<int>(blocks));
+    e = cudaGetLastError();
+  }
+  double tot[21];
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tot, scratch + static_cast<size_t>(kNoAllocBlocks) * 21, sizeof(tot),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess)
+    return noalloc_fail(HOMO_ECUDA, std::string("homo_CH_noalloc: ") + cudaGetErrorString(e));
+  const double invN = 1.0 / static_cast<double>(N);
+  int idx = 0;
+  for (int i = 0; i < kCases; ++i)
+    for (int j = i; j < kCases; ++j) {
+      CH[6 * i + j] = CH[6 * j + i] = tot[idx++] * invN;
+    }
+  return HOMO_OK;
+}
