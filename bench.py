@@ -47,6 +47,7 @@ def parse_args(argv=None):
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--sample-n", type=int, default=16, help="cell size of the oracle's CPU sample")
+    ap.add_argument("--sweeps", type=int, default=0, help="Gauss-Seidel sweeps before/after coarse correction (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args(argv)
@@ -233,7 +234,8 @@ def config_dict(args):
             "objective": args.objective, "volfrac": args.vf, "rel_tol": args.tol,
             "density": f"seeded blurred-noise inclusions (seed {args.seed}), exactly vf solid",
             "l2": "inputs larger than L2 (18 planes x n^3 fp32 per field)",
-            "parallelism": "replicas (one cell per GPU, no collective)"}
+            "parallelism": "replicas (one cell per GPU, no collective)",
+            "smoother": f"8-colour block Gauss-Seidel, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -271,7 +273,7 @@ def run_ours(args, rank, world, local):
     n = args.n
     rho0 = smoothed_threshold_density(n, args.vf, args.seed + rank)
     stream = torch.cuda.current_stream(dev)
-    hom = binding.Homogenization(n, stream=stream.cuda_stream)
+    hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream)
     r = torch.from_numpy(rho0).to(dev)
     rt = torch.empty_like(r)
     s = torch.empty_like(r)

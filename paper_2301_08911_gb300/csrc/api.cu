@@ -143,11 +143,14 @@ int ensure_hierarchy(homo_ctx* c) {
   return HOMO_OK;
 }
 
-int smooth_level(homo_ctx* c, int l, bool reverse, const float* f, float* x) {
+// One 8-colour sweep. first: the sweep starts from x = 0 (x need not be cleared; only
+// valid with colours in increasing order).
+int smooth_level(homo_ctx* c, int l, bool reverse, const float* f, float* x, bool first = false) {
+  const int fz = first && !reverse ? 1 : 0;
   for (int k = 0; k < 8; ++k) {
     const int col = reverse ? 7 - k : k;
-    if (l == 0) KL(c, HOMO_KC_FINE_GS, 1, launch_fine_gs(c, col, f, x));
-    else KL(c, HOMO_KC_COARSE_GS, 1, launch_coarse_gs(c->lev[l], col, f, x, c->stream));
+    if (l == 0) KL(c, HOMO_KC_FINE_GS, 1, launch_fine_gs(c, col, f, x, fz));
+    else KL(c, HOMO_KC_COARSE_GS, 1, launch_coarse_gs(c->lev[l], col, f, x, fz, c->stream));
   }
   return HOMO_OK;
 }
@@ -161,15 +164,15 @@ int vcycle(homo_ctx* c, const float* r, float* z) {
     return HOMO_OK;
   }
   const int pre = c->opts.pre_sweeps, post = c->opts.post_sweeps;
-  CK(c, cudaMemsetAsync(z, 0, sizeof(float) * kPlanes * c->N, s));
-  for (int k = 0; k < pre; ++k) RET(smooth_level(c, 0, false, r, z));
+  if (pre == 0) CK(c, cudaMemsetAsync(z, 0, sizeof(float) * kPlanes * c->N, s));
+  for (int k = 0; k < pre; ++k) RET(smooth_level(c, 0, false, r, z, k == 0));
   KL(c, HOMO_KC_FINE_RESIDUAL, 1, launch_fine_residual(c, r, z, nullptr, c->q, nullptr, nullptr));
   KL(c, HOMO_KC_TRANSFER, 1, launch_restrict(c->n, c->q, c->lev[1].b, s));
   const int L = c->nlev - 1;
   for (int l = 1; l < L; ++l) {
     Level& lv = c->lev[l];
-    CK(c, cudaMemsetAsync(lv.x, 0, sizeof(float) * kPlanes * lv.N, s));
-    for (int k = 0; k < pre; ++k) RET(smooth_level(c, l, false, lv.b, lv.x));
+    if (pre == 0) CK(c, cudaMemsetAsync(lv.x, 0, sizeof(float) * kPlanes * lv.N, s));
+    for (int k = 0; k < pre; ++k) RET(smooth_level(c, l, false, lv.b, lv.x, k == 0));
     KL(c, HOMO_KC_COARSE_RESIDUAL, 1, launch_coarse_residual(lv, lv.b, lv.x, lv.t, s));
     KL(c, HOMO_KC_TRANSFER, 1, launch_restrict(lv.n, lv.t, c->lev[l + 1].b, s));
   }
@@ -333,7 +336,8 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
   }
   if (rc == HOMO_OK) rc = dalloc(c, &c->A, static_cast<size_t>(c->mc) * c->mc, "coarsest A");
   if (rc == HOMO_OK) rc = dalloc(c, &c->G, static_cast<size_t>(c->mc) * c->mc, "coarsest G");
-  c->part_cap = static_cast<size_t>(16 * 152) * 32;
+  c->part_cap = std::max(static_cast<size_t>(16 * 152) * 32,
+                         static_cast<size_t>(tiled_grid_blocks(n)) * (kCases + kPlanes));
   if (rc == HOMO_OK) rc = dalloc(c, &c->part, c->part_cap, "partials");
   if (rc == HOMO_OK) rc = dalloc(c, &c->scal, static_cast<size_t>(S_COUNT), "scalars");
   if (rc == HOMO_OK) {
@@ -455,7 +459,7 @@ int homo_solve_cases(homo_ctx* ctx, double rel_tol, int max_iters, int warm_star
       ++total;
       for (int k = 0; k < kCases; ++k)
         if (c->hscal[S_FF + k] > 0.0 && c->hscal[S_RR + k] > rel_tol * rel_tol * c->hscal[S_FF + k]) ++its[k];
-      KL(c, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(c, c->pv, c->q, 1, c->part, &g));
+      KL(c, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(c, c->pv, c->q, c->part, &g));
       KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_PQ, c->stream));
       KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_alpha(c->scal, c->stream));
       KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_update_xr(c->u, c->ulo, c->r, c->pv, c->q, c->scal, c->N, c->part, &g, c->stream));
@@ -596,7 +600,7 @@ int homo_get_loads(homo_ctx* ctx, float* f) {
 int homo_apply_K(homo_ctx* ctx, const float* u, float* out) {
   if (!ctx || !u || !out || u == out) return HOMO_EINVAL;
   if (!ctx->density_set) return set_err(ctx, HOMO_ESTATE, "no density set");
-  KL(ctx, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(ctx, u, out, 1, nullptr, nullptr));
+  KL(ctx, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(ctx, u, out, nullptr, nullptr));
   return HOMO_OK;
 }
 

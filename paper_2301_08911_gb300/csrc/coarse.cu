@@ -140,10 +140,13 @@ __device__ __forceinline__ void solve3x6c(const float (&S)[9], float (&b)[18]) {
   }
 }
 
-// One colour pass of block Gauss-Seidel (Eq. 15-16) with the stored stencil.
+// One colour pass of block Gauss-Seidel (Eq. 15-16) with the stored stencil. Neighbours
+// have other colours and are not written during the pass. first != 0: first sweep from
+// x = 0 in colour order 0..7 (higher-colour neighbours are still zero and skipped).
 __global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
                                                    const float* __restrict__ f,
-                                                   float* __restrict__ x, int n, int colour) {
+                                                   float* __restrict__ x, int n, int colour,
+                                                   int first) {
   const size_t N = static_cast<size_t>(n) * n * n;
   const int h = n >> 1;
   const size_t Nh = static_cast<size_t>(h) * h * h;
@@ -166,13 +169,17 @@ __global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
     for (int d = 0; d < 27; ++d) {
       if (d == 13) continue;
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const int odd = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+      if (first && (colour ^ odd) > colour) continue;
       float A[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) A[q] = __ldg(st + static_cast<size_t>(9 * d + q) * N + p);
       const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+      const float* xr = x;
 #pragma unroll
       for (int c = 0; c < kCases; ++c) {
-        const float u0 = x[(3 * c) * N + w], u1 = x[(3 * c + 1) * N + w], u2 = x[(3 * c + 2) * N + w];
+        const float u0 = __ldg(xr + (3 * c) * N + w), u1 = __ldg(xr + (3 * c + 1) * N + w),
+                    u2 = __ldg(xr + (3 * c + 2) * N + w);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
           rhs[3 * c + r] -= fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, A[3 * r + 2] * u2));
@@ -427,10 +434,10 @@ cudaError_t launch_coarse_residual(const Level& L, const float* b, const float* 
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x,
+cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x, int first,
                              cudaStream_t s) {
   const size_t h = static_cast<size_t>(L.n / 2);
-  k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.st, f, x, L.n, colour);
+  k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.st, f, x, L.n, colour, first);
   return cudaGetLastError();
 }
 

@@ -62,81 +62,17 @@ __device__ __forceinline__ void solve3x6(const float (&S)[9], float (&b)[18]) {
   }
 }
 
-// Modes: 0 out = K u; 1 out = K u in difference form, + optional partials of the dots
-//        (u_c, out_c) and of the 18 plane sums of out; 3 out = b - K u.
-// The difference form uses sum_d A_d = 0 (rows of K annihilate translations) to apply
-// K to u_(v+d) - u_v, so large smooth fields lose no precision to cancellation.
-template <int MODE>
-__global__ void __launch_bounds__(256) k_fine_apply(const __grid_constant__ KeParam K,
-                                                    const float* __restrict__ E,
-                                                    const float* __restrict__ u,
-                                                    const float* __restrict__ ulo,
-                                                    const float* __restrict__ b,
-                                                    float* __restrict__ out, int n,
-                                                    double* __restrict__ part) {
-  const size_t N = static_cast<size_t>(n) * n * n;
-  float red[kCases + kPlanes];
-#pragma unroll
-  for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
-              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
-    const Nb nb = make_nb(x, y, z, n);
-    float Et[8];
-    load_E8(E, nb, Et);
-    float acc[kPlanes];
-#pragma unroll
-    for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
-    float own[kPlanes];
-    if (MODE == 1) {
-#pragma unroll
-      for (int q = 0; q < kPlanes; ++q) own[q] = __ldg(u + q * N + v);
-    }
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-      if (MODE == 1 && d == 13) continue;
-      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-      float A[9];
-      nb_block(K, Et, dx, dy, dz, A);
-      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
-#pragma unroll
-      for (int c = 0; c < kCases; ++c) {
-        float uu[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const size_t o = static_cast<size_t>(3 * c + k) * N + w;
-          if (MODE == 1) uu[k] = __ldg(u + o) - own[3 * c + k];
-          else uu[k] = __ldg(u + o);
-        }
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-          acc[3 * c + r] = fmaf(A[3 * r], uu[0], fmaf(A[3 * r + 1], uu[1], fmaf(A[3 * r + 2], uu[2], acc[3 * c + r])));
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < kCases; ++c)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const size_t o = static_cast<size_t>(3 * c + k) * N + v;
-        float val = acc[3 * c + k];
-        if (MODE == 3) val = __ldg(b + o) - val;
-        out[o] = val;
-        if (MODE == 1) {
-          red[c] = fmaf(own[3 * c + k], val, red[c]);
-          red[kCases + 3 * c + k] += val;
-        }
-      }
-  }
-  if (MODE == 1 && part != nullptr) block_sum_store<kCases + kPlanes>(red, part);
-}
-
 // One colour pass of 8-colour block Gauss-Seidel (Eq. 15-16): for every vertex v of
 // the colour, S_v u_v = f_v - M_v with S_v = A_0 and M_v = sum_(d != 0) A_d u_(v+d).
-__global__ void __launch_bounds__(256) k_fine_gs(const __grid_constant__ KeParam K,
+// The neighbour v + d has colour (colour XOR oddness-mask of d), never the pass's own
+// colour, so its value is not written during the pass (read through the read-only
+// path). first != 0: first sweep from u = 0 in colour order 0..7, where neighbours of a
+// higher colour still hold zero and are skipped (u need not be cleared beforehand).
+__global__ void __launch_bounds__(256, 3) k_fine_gs(const __grid_constant__ KeParam K,
                                                  const float* __restrict__ E,
                                                  const float* __restrict__ f,
-                                                 float* __restrict__ u, int n, int colour) {
+                                                 float* __restrict__ u, int n, int colour,
+                                                 int first) {
   const size_t N = static_cast<size_t>(n) * n * n;
   const int h = n >> 1;
   const size_t Nh = static_cast<size_t>(h) * h * h;
@@ -159,12 +95,16 @@ __global__ void __launch_bounds__(256) k_fine_gs(const __grid_constant__ KeParam
     for (int d = 0; d < 27; ++d) {
       if (d == 13) continue;
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const int odd = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+      if (first && (colour ^ odd) > colour) continue;
       float A[9];
       nb_block(K, Et, dx, dy, dz, A);
       const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+      const float* ur = u;
 #pragma unroll
       for (int c = 0; c < kCases; ++c) {
-        const float u0 = u[(3 * c) * N + w], u1 = u[(3 * c + 1) * N + w], u2 = u[(3 * c + 2) * N + w];
+        const float u0 = __ldg(ur + (3 * c) * N + w), u1 = __ldg(ur + (3 * c + 1) * N + w),
+                    u2 = __ldg(ur + (3 * c + 2) * N + w);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
           rhs[3 * c + r] -= fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, A[3 * r + 2] * u2));
@@ -434,15 +374,9 @@ cudaError_t launch_loads(const homo_ctx* c, float* f) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, int diff,
-                              double* part, int* grid_out) {
-  const int g = grid_for(c->N, 256);
-  if (grid_out) *grid_out = g;
-  if (diff)
-    k_fine_apply<1><<<g, 256, 0, c->stream>>>(c->ke, c->E, u, nullptr, nullptr, out, c->n, part);
-  else
-    k_fine_apply<0><<<g, 256, 0, c->stream>>>(c->ke, c->E, u, nullptr, nullptr, out, c->n, nullptr);
-  return cudaGetLastError();
+cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, double* part,
+                              int* grid_out) {
+  return launch_fine_tiled(c, 1, u, nullptr, out, part, grid_out);
 }
 
 cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float* u,
@@ -451,17 +385,14 @@ cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float*
     const int g = grid_for(c->N, 128);
     if (grid_out) *grid_out = g;
     k_fine_true_residual<<<g, 128, 0, c->stream>>>(c->ke, c->E, u, ulo, b, out, c->n, part);
-  } else {
-    const int g = grid_for(c->N, 256);
-    if (grid_out) *grid_out = g;
-    k_fine_apply<3><<<g, 256, 0, c->stream>>>(c->ke, c->E, u, nullptr, b, out, c->n, nullptr);
+    return cudaGetLastError();
   }
-  return cudaGetLastError();
+  return launch_fine_tiled(c, 3, u, b, out, nullptr, grid_out);
 }
 
-cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u) {
+cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first) {
   const size_t h = static_cast<size_t>(c->n / 2);
-  k_fine_gs<<<grid_for(h * h * h, 256), 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour);
+  k_fine_gs<<<grid_for(h * h * h, 256), 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour, first);
   return cudaGetLastError();
 }
 

@@ -149,14 +149,20 @@ int build_filter_param(double radius, FilterParam& fp);
 cudaError_t launch_simp(const float* rho_in, float* rho_out, float* E, size_t N, float p,
                         float E0, float Emin, cudaStream_t s);
 cudaError_t launch_loads(const homo_ctx* c, float* f);
-// out = K u (diff form if diff != 0) on level 0; if pq != nullptr also block partials of
-// (u_c, out_c) into part (grid * 6 doubles) and returns the grid size in *grid_out.
-cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, int diff,
+// out = K u on level 0 in difference form; if part != nullptr also block partials of the
+// dots (u_c, out_c) and the 18 plane sums of out (24 doubles per block; *grid_out blocks).
+cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, double* part,
+                              int* grid_out);
+// tiled finest-level stencil (fine_tiled.cu): mode 1 = launch_fine_apply, mode 3 = b - K u
+cudaError_t launch_fine_tiled(const homo_ctx* c, int mode, const float* u, const float* b, float* out,
                               double* part, int* grid_out);
+size_t tiled_smem_bytes();
+int tiled_grid_blocks(int n);
 // out = b - K (u + ulo) in difference form (accurate true residual); partials of ||out_c||^2.
 cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float* u,
                                  const float* ulo, float* out, double* part, int* grid_out);
-cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u);
+// first != 0: first sweep from u = 0, colours 0..7 (u need not be cleared)
+cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first);
 cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, float* sens,
                              double* part, int* grid_out);
 
@@ -165,7 +171,7 @@ cudaError_t launch_level1_assemble(const homo_ctx* c, const Level& L1);
 cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, cudaStream_t s);
 cudaError_t launch_coarse_residual(const Level& L, const float* b, const float* x, float* out,
                                    cudaStream_t s);
-cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x,
+cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x, int first,
                              cudaStream_t s);
 cudaError_t launch_restrict(int nf, const float* fine, float* coarse, cudaStream_t s);
 cudaError_t launch_prolong_add(int nf, const float* coarse, float* fine, int overwrite,
