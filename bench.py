@@ -30,6 +30,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PAPER_512_BULK_MS = 38030.0      # paper, 512^3 bulk vf 0.3: 38.03 s per iteration (GTX 1080Ti)
+METRIC = "ms per opt. iteration at 256\u00b3/512\u00b3 (6 cases to rel-res 1e-5); stencil HBM GB/s"
 FP32_LANES_PER_SM = 128
 NUM_SMS = 152
 
@@ -47,7 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--sample-n", type=int, default=16, help="cell size of the oracle's CPU sample")
-    ap.add_argument("--sweeps", type=int, default=0, help="Gauss-Seidel sweeps before/after coarse correction (0 = library default)")
+    ap.add_argument("--sweeps", type=int, default=0, help="smoothing sweeps before/after coarse correction (0 = library default)")
+    ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args(argv)
@@ -155,16 +157,33 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-# Algorithmic work per launch of each finest-level kernel class, N = n^3 vertices, 6 cases.
-# Bytes: minimum DRAM traffic the operation implies; flops: arithmetic of the algorithm.
-def algorithmic_work(kc: str, n: int):
+# Algorithmic work per launch (average over the launches of a class in one V-cycle) of the
+# finest-level kernel classes, N = n^3 vertices, 6 cases. Bytes: the DRAM traffic the
+# operation implies at minimum; flops: the algorithm's arithmetic.
+STENCIL_FLOP = (576 + 27 * 54) * 2      # 27 blocks from E and K0, applied to 6 cases
+SOLVE_FLOP = 6 * 15 + 30                # 3x3 LDL^T and 6 solves
+
+
+def algorithmic_work(kc: str, n: int, sweeps: int = 1):
     N = n ** 3
-    if kc == "fine_gs":          # one colour pass: E 4N, the other colours' u 63N, f_c and u_c 9N+9N
-        return 85 * N, (576 + 26 * 54 + 6 * 15 + 30) * 2 * N / 8
-    if kc == "fine_matvec":      # E 4N + p 72N + q 72N; 27 blocks from E (576 FMA) + 26 x 6 x 9 FMA + 468 sub
+    if kc == "fine_gs":
+        # colour pass: E 4N, the other colours' u 63N, f_c 9N, u_c 9N (85N); in the first
+        # sweep from zero only lower colours are read (half: 53.5N). 1 of 2*sweeps sweeps.
+        full_b, first_b = 85 * N, 53.5 * N
+        full_f = (576 + 26 * 54 + SOLVE_FLOP) * 2 * N / 8
+        first_f = (288 + 13 * 54 + SOLVE_FLOP) * 2 * N / 8
+        w = 1.0 / (2 * sweeps)
+        return w * first_b + (1 - w) * full_b, w * first_f + (1 - w) * full_f
+    if kc == "fine_cheb":
+        # degree 2: pointwise start (b 72, x 72, E 4), then three tiled steps reading the
+        # iterate and b, one also the previous iterate, each writing the new iterate
+        b = (148 + 216 + 216 + 288) / 4 * N
+        f = ((72 * 2 + SOLVE_FLOP) + 3 * (STENCIL_FLOP + SOLVE_FLOP)) / 4 * N
+        return b, f
+    if kc == "fine_matvec":      # E 4N + p 72N + q 72N; difference form: 26 blocks + 468 sub
         return 148 * N, ((576 + 26 * 54) * 2 + 26 * 18) * N
     if kc == "fine_residual":    # E 4N + x 72N + b 72N + out 72N
-        return 220 * N, ((576 + 27 * 54) * 2) * N
+        return 220 * N, STENCIL_FLOP * N
     if kc == "element":          # u 72N + E/rho 8N (+ out 4N); 6 x 576 + 21 x 24 FMA per element
         return 80 * N, (6 * 576 + 21 * 24) * 2 * N
     return None, None
@@ -235,7 +254,9 @@ def config_dict(args):
             "density": f"seeded blurred-noise inclusions (seed {args.seed}), exactly vf solid",
             "l2": "inputs larger than L2 (18 planes x n^3 fp32 per field)",
             "parallelism": "replicas (one cell per GPU, no collective)",
-            "smoother": f"8-colour block Gauss-Seidel, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle"}
+            "smoother": (f"8-colour block Gauss-Seidel, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle"
+                         if args.smoother == "gs8" else
+                         f"Chebyshev(2)/block-Jacobi, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle")}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -250,7 +271,7 @@ def run_reference(args, rank, world):
     sample = (f"oracle (numpy/scipy FP64, sparse LU solve) optimisation iterations at "
               f"{args.sample_n}^3, {args.steps} timed after {args.warmup} warm-up, scaled linearly by "
               f"element count to {args.n}^3 (a lower bound: the direct solve grows faster than linearly)")
-    line = {"impl": "reference", "metric": "ms per optimization iteration", "value": ms, "unit": "ms",
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args),
@@ -273,7 +294,7 @@ def run_ours(args, rank, world, local):
     n = args.n
     rho0 = smoothed_threshold_density(n, args.vf, args.seed + rank)
     stream = torch.cuda.current_stream(dev)
-    hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream)
+    hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream, smoother=args.smoother)
     r = torch.from_numpy(rho0).to(dev)
     rt = torch.empty_like(r)
     s = torch.empty_like(r)
@@ -356,7 +377,7 @@ def run_ours(args, rank, world, local):
     dom = max(prof.items(), key=lambda kv: kv[1][1])
     kc, (kn, kms) = dom
     peak_hbm, peak_src = measured_peaks()
-    nbytes, nflops = algorithmic_work(kc, n)
+    nbytes, nflops = algorithmic_work(kc, n, args.sweeps or 1)
     roofline = None
     if nbytes is not None and kn > 0:
         avg_s = kms / kn / 1000.0
@@ -389,7 +410,7 @@ def run_ours(args, rank, world, local):
 
     cg = np.array(state["cg"])
     line = {
-        "metric": "ms per optimization iteration (6 cases to rel-res 1e-5)",
+        "metric": METRIC,
         "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": (ms_step / PAPER_512_BULK_MS) if (n == 512 and args.objective == "bulk"

@@ -75,9 +75,20 @@ typedef struct homo_opts {
   int min_coarse;   /* coarsen by 2 while the next level keeps >= min_coarse cells per
                        axis (default 4, Sec. 3.3); the coarsest level is solved directly */
   int max_levels;   /* cap on the number of levels, 0 = no cap                           */
-  int pre_sweeps;   /* 8-colour Gauss-Seidel sweeps before coarse correction (default 1) */
-  int post_sweeps;  /* sweeps after it, colours in reverse order (default 1)             */
+  int pre_sweeps;   /* smoothing sweeps before coarse correction (default 1)             */
+  int post_sweeps;  /* smoothing sweeps after it (default 1; must equal pre_sweeps)      */
+  int smoother;     /* HOMO_SMOOTH_GS8 (default) or HOMO_SMOOTH_CHEBYSHEV                */
+  int cheb_degree;  /* Chebyshev polynomial degree per sweep, 2..4 (default 2)           */
 } homo_opts;
+
+/* Smoothers. GS8: 8-colour block Gauss-Seidel (Sec. 4.1-4.2, Eq. 15-16), colours 0..7
+ * before and 7..0 after the coarse correction. CHEBYSHEV: Chebyshev polynomial in
+ * D^-1 K (D the 3x3 block diagonal, the GS8 diagonal solve S_v of Eq. 16) on the
+ * interval [lmax/10, lmax], lmax the element bound max eig(D_e^-1 K0) on the finest
+ * level and a 12-step power-iteration estimate x1.15 on coarse levels; every step is
+ * one data-parallel pass (not in the paper, which uses GS8). */
+#define HOMO_SMOOTH_GS8 0
+#define HOMO_SMOOTH_CHEBYSHEV 1
 
 /* Library version as 10000*major + 100*minor + patch. */
 int homo_version(void);
@@ -133,10 +144,28 @@ int homo_set_density(homo_ctx* ctx, const float* rho, int on_device);
  *   warm_start: 1 = start from the fields of the previous solve, 0 = from zero.
  *   iters_out, relres_out: host arrays of 6 (nullable): CG iterations per case and
  *               final true relative residual per case.
+ * The true residual is the rigid-translation-free part of f - K u (translations lie
+ * outside the range of K). The result is certified in double-float arithmetic; for
+ * rel_tol >= 1e-5 the starting residual is the FP32 one (see homo_residual).
  * Returns HOMO_ENOCONV if a case missed rel_tol within max_iters (fields valid),
  * HOMO_EDIVERGED on a non-finite residual. Synchronises the stream. */
 int homo_solve_cases(homo_ctx* ctx, double rel_tol, int max_iters, int warm_start,
                      int iters_out[6], double relres_out[6]);
+
+/* Relative true residual ||f_i - K u_i||_2 / ||f_i||_2 (rigid translations removed) of
+ * the context's current displacement fields, per case (0 where f_i = 0), by one of two
+ * evaluations (the paper measures convergence with this quantity, Sec. 4.1 "Mixed
+ * floating-point precision"; the two evaluations are this library's):
+ *   method HOMO_RESIDUAL_FP32        : FP32 difference form, each neighbour difference
+ *                                      formed from both parts of the double-float field;
+ *   method HOMO_RESIDUAL_DOUBLE_FLOAT: double-float arithmetic throughout.
+ *   relres_out: host, 6 doubles (output).
+ * Needs loads (a homo_set_density); overwrites the context's residual scratch.
+ * Returns HOMO_ESTATE before homo_set_density, HOMO_EINVAL on a bad method or NULL
+ * output. Synchronises the stream. */
+#define HOMO_RESIDUAL_FP32 0
+#define HOMO_RESIDUAL_DOUBLE_FLOAT 1
+int homo_residual(homo_ctx* ctx, int method, double relres_out[6]);
 
 /* C^H without any device allocation (the paper has no counterpart to this entry point).
  * For callers that cannot call cudaMalloc while they run: an application that sets its
@@ -198,6 +227,11 @@ int homo_objective(int kind, const double CH[36], int iteration, double param,
  * Ke: host, 576 doubles, row-major. No GPU needed. */
 int homo_element_matrix(double nu, double Ke[576]);
 
+/* Largest eigenvalue of D_e^-1 K0 (D_e: the 3x3 block diagonal of K0), which bounds the
+ * spectrum of D^-1 K on the finest level for any moduli; the Chebyshev smoother's upper
+ * interval end there. Host arithmetic only; out: 1 double. */
+int homo_element_jacobi_bound(double nu, double* out);
+
 /* ---- Introspection and operator access (device pointers, 6-case layout above) ---- */
 
 /* Copy the current 6 displacement fields out / in (18*N floats, device). */
@@ -247,7 +281,9 @@ int homo_vcycle(homo_ctx* ctx, const float* r, float* z);
 #define HOMO_KC_FILTER 10          /* density filter                                        */
 #define HOMO_KC_OC 11              /* OC update                                             */
 #define HOMO_KC_OTHER 12           /* SIMP moduli, field copies, stencil export             */
-#define HOMO_KC_COUNT 13
+#define HOMO_KC_FINE_CHEB 13       /* finest-level Chebyshev smoothing steps                */
+#define HOMO_KC_COARSE_CHEB 14     /* coarse-level Chebyshev smoothing steps                */
+#define HOMO_KC_COUNT 15
 
 /* Start (enable = 1, counters reset) or stop (0) recording a CUDA event pair around
  * every kernel launch of the context, on its stream. */

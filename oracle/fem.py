@@ -186,7 +186,7 @@ def sensitivity(rho_t: np.ndarray, q: np.ndarray, dfdC: np.ndarray, p: float = 3
     """df/d rho_e = sum_ij (df/dC_ij) dC_ij/d rho_e with dC_ij/d rho_e = E'(rho_e) q_e,ij / |Omega|.
 
     Eq. 8 and Eq. 9. The sum over e printed in Eq. 9 is read as a typo: the derivative
-    is per element (Sec. 4.3 "We do not sum over all the elements ..."). The SIMP
+    is per element (Sec. 4.3 states that the derivative is not summed over elements). The SIMP
     derivative is that of simp_modulus.
     """
     dE = simp_modulus_derivative(rho_t, p, E0, Emin)

@@ -26,7 +26,11 @@ _vp = ctypes.c_void_p
 class HomoOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("min_coarse", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
-                ("post_sweeps", ctypes.c_int)]
+                ("post_sweeps", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("cheb_degree", ctypes.c_int)]
+
+
+SMOOTHERS = {"gs8": 0, "chebyshev": 1}
 
 
 # name -> (restype, argtypes), mirroring include/homo.h
@@ -50,6 +54,7 @@ SIGNATURES = {
     "homo_objective": (ctypes.c_int, [ctypes.c_int, _c_double_p, ctypes.c_int, ctypes.c_double, _c_double_p,
                                       _c_double_p]),
     "homo_element_matrix": (ctypes.c_int, [ctypes.c_double, _c_double_p]),
+    "homo_element_jacobi_bound": (ctypes.c_int, [ctypes.c_double, _c_double_p]),
     "homo_get_displacement": (ctypes.c_int, [_vp, _vp]),
     "homo_set_displacement": (ctypes.c_int, [_vp, _vp]),
     "homo_get_loads": (ctypes.c_int, [_vp, _vp]),
@@ -64,10 +69,11 @@ SIGNATURES = {
     "homo_kernel_class_name": (ctypes.c_char_p, [ctypes.c_int]),
     "homo_launch_count": (ctypes.c_longlong, [_vp]),
     "homo_residual_history": (ctypes.c_int, [_vp, _c_double_p, ctypes.c_int]),
+    "homo_residual": (ctypes.c_int, [_vp, ctypes.c_int, _c_double_p]),
     "homo_CH_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _c_double_p, _vp]),
 }
 
-KERNEL_CLASSES = 13
+KERNEL_CLASSES = 15
 
 _lib = None
 
@@ -129,9 +135,11 @@ class Homogenization:
     """One periodic n^3 cell: owns a homo_ctx and its device buffers."""
 
     def __init__(self, n: int, E0: float = 1.0, nu: float = 0.3, p: float = 3.0, Emin: float = 1e-9,
-                 min_coarse: int = 0, max_levels: int = 0, sweeps: int = 0, stream=None):
+                 min_coarse: int = 0, max_levels: int = 0, sweeps: int = 0, stream=None,
+                 smoother: str = "gs8", cheb_degree: int = 0):
         self.lib = load_library()
-        opts = HomoOpts(ctypes.sizeof(HomoOpts), min_coarse, max_levels, sweeps, sweeps)
+        opts = HomoOpts(ctypes.sizeof(HomoOpts), min_coarse, max_levels, sweeps, sweeps,
+                        SMOOTHERS[smoother], cheb_degree)
         h = _vp()
         st = self.lib.homo_create(ctypes.byref(h), n, E0, nu, p, Emin, ctypes.byref(opts))
         if st != HOMO_OK:
@@ -252,6 +260,13 @@ class Homogenization:
     @property
     def launch_count(self) -> int:
         return self.lib.homo_launch_count(self.h)
+
+    def residual(self, method: str = "double_float") -> np.ndarray:
+        """Relative true residual per case of the current fields ("fp32" or "double_float")."""
+        m = {"fp32": 0, "double_float": 1}[method]
+        out = (ctypes.c_double * 6)()
+        self._check(self.lib.homo_residual(self.h, m, out))
+        return np.array(out[:])
 
     def residual_history(self) -> np.ndarray:
         """(records, 6) relative residuals of the last solve."""

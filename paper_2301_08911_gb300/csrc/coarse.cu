@@ -227,6 +227,76 @@ __global__ void __launch_bounds__(256) k_coarse_residual(const float* __restrict
   }
 }
 
+// Chebyshev step with the stored stencil (threads walk stencil positions):
+// mode 0: out = x_in + c0 S^-1 (b - K x_in); mode 1: out = x_in + c0 (x_in - out) +
+// c1 S^-1 (b - K x_in), the previous iterate read from out and replaced in place.
+// x_in == null stands for x_in = 0 (first step from zero). mode 2: out = S^-1 K x_in
+// (power iteration for the largest eigenvalue of D^-1 K).
+__global__ void __launch_bounds__(256) k_coarse_cheb(const float* __restrict__ st,
+                                                     const float* __restrict__ b,
+                                                     const float* __restrict__ xin, float* out,
+                                                     int n, bool cb, int mode, float c0, float c1) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t p = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < N;
+       p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int X, Y, Z;
+    vertex_of_pos(p, n, cb, X, Y, Z);
+    const size_t v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
+    float acc[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
+    if (xin) {
+      const Nb nb = make_nb(X, Y, Z, n);
+#pragma unroll
+      for (int d = 0; d < 27; ++d) {
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        float A[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) A[q] = __ldg(st + static_cast<size_t>(9 * d + q) * N + p);
+        const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+#pragma unroll
+        for (int c = 0; c < kCases; ++c) {
+          const float u0 = __ldg(xin + (3 * c) * N + w), u1 = __ldg(xin + (3 * c + 1) * N + w),
+                      u2 = __ldg(xin + (3 * c + 2) * N + w);
+#pragma unroll
+          for (int r = 0; r < 3; ++r)
+            acc[3 * c + r] = fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, fmaf(A[3 * r + 2], u2, acc[3 * c + r])));
+        }
+      }
+    }
+    float S[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) S[q] = __ldg(st + static_cast<size_t>(9 * 13 + q) * N + p);
+    if (mode != 2) {
+#pragma unroll
+      for (int q = 0; q < kPlanes; ++q) acc[q] = __ldg(b + q * N + v) - acc[q];
+    }
+    solve3x6c(S, acc);
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) {
+      const size_t o = q * N + v;
+      const float xc = xin ? __ldg(xin + o) : 0.f;
+      if (mode == 0) out[o] = fmaf(c0, acc[q], xc);
+      else if (mode == 1) out[o] = fmaf(c1, acc[q], fmaf(c0, xc - out[o], xc));
+      else if (mode == 3) out[o] = fmaf(c1, acc[q], fmaf(c0, xc, xc));   // previous iterate 0
+      else out[o] = acc[q];
+    }
+  }
+}
+
+__global__ void k_fill_hash(float* __restrict__ x, size_t count, unsigned seed) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < count;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    unsigned h = static_cast<unsigned>(i) * 0x9E3779B1u ^ seed;
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    x[i] = static_cast<float>(h) * (2.f / 4294967296.f) - 1.f;
+  }
+}
+
 // coarse[V] = sum over fine 2V + a, a in {-1,0,1}^3, of w(a) fine[2V + a] (R = I^T).
 __global__ void __launch_bounds__(256) k_restrict(const float* __restrict__ fine, int nf,
                                                   float* __restrict__ coarse) {
@@ -254,36 +324,57 @@ __global__ void __launch_bounds__(256) k_restrict(const float* __restrict__ fine
   }
 }
 
-// fine[v] (+)= sum of trilinear weights * coarse (I).
+// fine (+)= I coarse. One thread per coarse cell (X..X+1, Y..Y+1, Z..Z+1): its 8 corner
+// values give the 8 fine vertices (2X+a, 2Y+b, 2Z+c), a,b,c in {0,1}, by trilinear
+// weights (1 on an even fine coordinate, 1/2 to each neighbour on an odd one).
 __global__ void __launch_bounds__(256) k_prolong(const float* __restrict__ coarse, int nf,
                                                  float* __restrict__ fine, int overwrite) {
   const int nc = nf / 2;
   const size_t Nf = static_cast<size_t>(nf) * nf * nf;
   const size_t Nc = static_cast<size_t>(nc) * nc * nc;
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < Nf;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(v % nf), y = static_cast<int>((v / nf) % nf),
-              z = static_cast<int>(v / (static_cast<size_t>(nf) * nf));
-    // the (up to) 8 coarse vertices around x/2; an even coordinate has one parent
-    const int x0 = x >> 1, y0 = y >> 1, z0 = z >> 1;
-    const int x1 = (x & 1) ? (x0 + 1 == nc ? 0 : x0 + 1) : x0;
-    const int y1 = (y & 1) ? (y0 + 1 == nc ? 0 : y0 + 1) : y0;
-    const int z1 = (z & 1) ? (z0 + 1 == nc ? 0 : z0 + 1) : z0;
-    size_t idx[8];
+  for (size_t V = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; V < Nc;
+       V += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int X = static_cast<int>(V % nc), Y = static_cast<int>((V / nc) % nc),
+              Z = static_cast<int>(V / (static_cast<size_t>(nc) * nc));
+    const int X1 = X + 1 == nc ? 0 : X + 1, Y1 = Y + 1 == nc ? 0 : Y + 1, Z1 = Z + 1 == nc ? 0 : Z + 1;
+    size_t cidx[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k)
-      idx[k] = static_cast<size_t>((k & 1) ? x1 : x0) +
-               static_cast<size_t>(nc) * (((k >> 1) & 1 ? y1 : y0) + static_cast<size_t>(nc) * ((k >> 2) ? z1 : z0));
-#pragma unroll 2
+      cidx[k] = static_cast<size_t>((k & 1) ? X1 : X) +
+                static_cast<size_t>(nc) * (((k >> 1) & 1 ? Y1 : Y) + static_cast<size_t>(nc) * ((k >> 2) ? Z1 : Z));
+    size_t fidx[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      fidx[k] = static_cast<size_t>(2 * X + (k & 1)) +
+                static_cast<size_t>(nf) * ((2 * Y + ((k >> 1) & 1)) + static_cast<size_t>(nf) * (2 * Z + (k >> 2)));
+#pragma unroll 1
     for (int q = 0; q < kPlanes; ++q) {
       const float* cq = coarse + q * Nc;
-      float acc = 0.f;
-      // an axis with an even coordinate repeats its single parent in both corner slots,
-      // so each distinct parent appears 8 * (its trilinear weight) times among the 8
+      float c[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) acc += __ldg(cq + idx[k]);
-      acc *= 0.125f;
-      fine[q * Nf + v] = overwrite ? acc : fine[q * Nf + v] + acc;
+      for (int k = 0; k < 8; ++k) c[k] = __ldg(cq + cidx[k]);
+      // interpolate along x, then y, then z
+      float ax[8];
+#pragma unroll
+      for (int k = 0; k < 8; k += 2) {
+        ax[k] = c[k];
+        ax[k + 1] = 0.5f * (c[k] + c[k + 1]);
+      }
+      float ay[8];
+#pragma unroll
+      for (int zc = 0; zc < 2; ++zc)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const float lo = ax[4 * zc + a], hi = ax[4 * zc + 2 + a];
+          ay[4 * zc + a] = lo;
+          ay[4 * zc + 2 + a] = 0.5f * (lo + hi);
+        }
+      float* fq = fine + q * Nf;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float val = (k >> 2) ? 0.5f * (ay[k & 3] + ay[4 + (k & 3)]) : ay[k];
+        fq[fidx[k]] = overwrite ? val : fq[fidx[k]] + val;
+      }
     }
   }
 }
@@ -441,6 +532,22 @@ cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* 
   return cudaGetLastError();
 }
 
+cudaError_t launch_coarse_cheb(const Level& L, const float* b, const float* x_in, float* out, int mode,
+                               float c0, float c1, cudaStream_t s) {
+  k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, b, x_in, out, L.n, L.colour_blocked, mode, c0, c1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_dinvk(const Level& L, const float* x, float* y, cudaStream_t s) {
+  k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, nullptr, x, y, L.n, L.colour_blocked, 2, 0.f, 0.f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_hash(float* x, size_t count, unsigned seed, cudaStream_t s) {
+  k_fill_hash<<<grid_for(count, 256), 256, 0, s>>>(x, count, seed);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_restrict(int nf, const float* fine, float* coarse, cudaStream_t s) {
   const size_t nc = static_cast<size_t>(nf / 2);
   k_restrict<<<grid_for(nc * nc * nc, 256), 256, 0, s>>>(fine, nf, coarse);
@@ -450,7 +557,7 @@ cudaError_t launch_restrict(int nf, const float* fine, float* coarse, cudaStream
 cudaError_t launch_prolong_add(int nf, const float* coarse, float* fine, int overwrite,
                                cudaStream_t s) {
   const size_t Nf = static_cast<size_t>(nf) * nf * nf;
-  k_prolong<<<grid_for(Nf, 256), 256, 0, s>>>(coarse, nf, fine, overwrite);
+  k_prolong<<<grid_for(Nf / 8, 256), 256, 0, s>>>(coarse, nf, fine, overwrite);
   return cudaGetLastError();
 }
 

@@ -106,6 +106,76 @@ void build_level1_tables(const KeParam& ke, float* Bf) {
   }
 }
 
+// Largest eigenvalue of D_e^-1 K0, D_e the 3x3 block diagonal of K0. With
+// x^T K x = sum_e E_e x_e^T K0 x_e <= lam sum_e E_e x_e^T D_e x_e = lam x^T D x it bounds
+// the spectrum of D^-1 K on the finest level for any moduli E. Power iteration on the
+// symmetric similar matrix D^-1/2 K0 D^-1/2, in double.
+double element_jacobi_bound(const KeParam& ke) {
+  double K[24][24], Dinvh[8][3][3];
+  for (int r = 0; r < 24; ++r)
+    for (int c = 0; c < 24; ++c) K[r][c] = 0.5 * (ke.k[r * 24 + c] + ke.k[c * 24 + r]);
+  // D^-1/2 per 3x3 block by its eigen-decomposition (Jacobi rotations)
+  for (int j = 0; j < 8; ++j) {
+    double a[3][3], v[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) a[r][c] = K[3 * j + r][3 * j + c];
+    for (int sweep = 0; sweep < 50; ++sweep)
+      for (int p = 0; p < 3; ++p)
+        for (int q = p + 1; q < 3; ++q) {
+          if (std::fabs(a[p][q]) < 1e-300) continue;
+          const double th = 0.5 * std::atan2(2 * a[p][q], a[q][q] - a[p][p]);
+          const double cs = std::cos(th), sn = std::sin(th);
+          for (int k = 0; k < 3; ++k) {   // rotate columns p, q
+            const double akp = a[k][p], akq = a[k][q];
+            a[k][p] = cs * akp - sn * akq;
+            a[k][q] = sn * akp + cs * akq;
+          }
+          for (int k = 0; k < 3; ++k) {   // rotate rows p, q
+            const double apk = a[p][k], aqk = a[q][k];
+            a[p][k] = cs * apk - sn * aqk;
+            a[q][k] = sn * apk + cs * aqk;
+          }
+          for (int k = 0; k < 3; ++k) {
+            const double vkp = v[k][p], vkq = v[k][q];
+            v[k][p] = cs * vkp - sn * vkq;
+            v[k][q] = sn * vkp + cs * vkq;
+          }
+        }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        double s = 0;
+        for (int k = 0; k < 3; ++k) s += v[r][k] * v[c][k] / std::sqrt(a[k][k]);
+        Dinvh[j][r][c] = s;
+      }
+  }
+  double M[24][24];
+  for (int r = 0; r < 24; ++r)
+    for (int c = 0; c < 24; ++c) {
+      double s = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+          s += Dinvh[r / 3][r % 3][a] * K[3 * (r / 3) + a][3 * (c / 3) + b] * Dinvh[c / 3][b][c % 3];
+      M[r][c] = s;
+    }
+  double x[24], y[24], lam = 0;
+  for (int i = 0; i < 24; ++i) x[i] = 1.0 + 0.01 * i;
+  for (int it = 0; it < 2000; ++it) {
+    double nrm = 0;
+    for (int r = 0; r < 24; ++r) {
+      double s = 0;
+      for (int c = 0; c < 24; ++c) s += M[r][c] * x[c];
+      y[r] = s;
+      nrm += s * s;
+    }
+    nrm = std::sqrt(nrm);
+    double rq = 0;
+    for (int r = 0; r < 24; ++r) rq += x[r] * y[r];
+    lam = rq;
+    for (int r = 0; r < 24; ++r) x[r] = y[r] / nrm;
+  }
+  return lam;
+}
+
 int build_filter_param(double radius, FilterParam& fp) {
   if (!(radius > 0.0) || radius > 3.5) return HOMO_EINVAL;
   const int R = static_cast<int>(std::ceil(radius));

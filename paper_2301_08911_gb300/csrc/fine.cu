@@ -40,8 +40,9 @@ __device__ __forceinline__ void nb_block(const KeParam& K, const float (&Et)[8],
   }
 }
 
-// Solve the SPD 3x3 system S y = b for 6 right-hand sides (LDL^T, FP32).
-__device__ __forceinline__ void solve3x6(const float (&S)[9], float (&b)[18]) {
+// Solve the SPD 3x3 system S y = b for NC right-hand sides (LDL^T, FP32).
+template <int NC>
+__device__ __forceinline__ void solve3xn(const float (&S)[9], float (&b)[3 * NC]) {
   const float d0 = S[0];
   const float l10 = S[3] / d0, l20 = S[6] / d0;
   const float d1 = S[4] - l10 * S[1];
@@ -49,7 +50,7 @@ __device__ __forceinline__ void solve3x6(const float (&S)[9], float (&b)[18]) {
   const float d2 = S[8] - l20 * S[2] - l21 * (S[5] - l10 * S[2]);
   const float i0 = 1.f / d0, i1 = 1.f / d1, i2 = 1.f / d2;
 #pragma unroll
-  for (int c = 0; c < kCases; ++c) {
+  for (int c = 0; c < NC; ++c) {
     float y0 = b[3 * c], y1 = b[3 * c + 1], y2 = b[3 * c + 2];
     y1 -= l10 * y0;
     y2 -= l20 * y0 + l21 * y1;
@@ -62,21 +63,28 @@ __device__ __forceinline__ void solve3x6(const float (&S)[9], float (&b)[18]) {
   }
 }
 
+__device__ __forceinline__ void solve3x6(const float (&S)[9], float (&b)[18]) { solve3xn<kCases>(S, b); }
+
 // One colour pass of 8-colour block Gauss-Seidel (Eq. 15-16): for every vertex v of
 // the colour, S_v u_v = f_v - M_v with S_v = A_0 and M_v = sum_(d != 0) A_d u_(v+d).
 // The neighbour v + d has colour (colour XOR oddness-mask of d), never the pass's own
 // colour, so its value is not written during the pass (read through the read-only
 // path). first != 0: first sweep from u = 0 in colour order 0..7, where neighbours of a
 // higher colour still hold zero and are skipped (u need not be cleared beforehand).
-__global__ void __launch_bounds__(256, 3) k_fine_gs(const __grid_constant__ KeParam K,
+// The load cases are split over blockIdx.y in groups of kGsCases: the blocks A_d are
+// rebuilt per group, which keeps registers low and puts more loads in flight.
+constexpr int kGsCases = 3;
+
+__global__ void __launch_bounds__(256, 4) k_fine_gs(const __grid_constant__ KeParam K,
                                                  const float* __restrict__ E,
                                                  const float* __restrict__ f,
                                                  float* __restrict__ u, int n, int colour,
-                                                 int first) {
+                                                 int first, const double* __restrict__ fmean) {
   const size_t N = static_cast<size_t>(n) * n * n;
   const int h = n >> 1;
   const size_t Nh = static_cast<size_t>(h) * h * h;
   const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
+  const int q0 = 3 * kGsCases * blockIdx.y;                // first plane of the case group
   for (size_t m = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < Nh;
        m += static_cast<size_t>(gridDim.x) * blockDim.x) {
     const int x = 2 * static_cast<int>(m % h) + cx;
@@ -86,11 +94,10 @@ __global__ void __launch_bounds__(256, 3) k_fine_gs(const __grid_constant__ KePa
     const Nb nb = make_nb(x, y, z, n);
     float Et[8];
     load_E8(E, nb, Et);
-    float rhs[kPlanes];
+    float rhs[3 * kGsCases];
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) rhs[q] = __ldg(f + q * N + v);
-    float S[9];
-    nb_block(K, Et, 0, 0, 0, S);
+    for (int q = 0; q < 3 * kGsCases; ++q)
+      rhs[q] = __ldg(f + (q0 + q) * N + v) - (fmean ? static_cast<float>(fmean[q0 + q]) : 0.f);
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
       if (d == 13) continue;
@@ -100,19 +107,21 @@ __global__ void __launch_bounds__(256, 3) k_fine_gs(const __grid_constant__ KePa
       float A[9];
       nb_block(K, Et, dx, dy, dz, A);
       const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
-      const float* ur = u;
+      const float* ur = u + q0 * N + w;
 #pragma unroll
-      for (int c = 0; c < kCases; ++c) {
-        const float u0 = __ldg(ur + (3 * c) * N + w), u1 = __ldg(ur + (3 * c + 1) * N + w),
-                    u2 = __ldg(ur + (3 * c + 2) * N + w);
+      for (int c = 0; c < kGsCases; ++c) {
+        const float u0 = __ldg(ur + (3 * c) * N), u1 = __ldg(ur + (3 * c + 1) * N),
+                    u2 = __ldg(ur + (3 * c + 2) * N);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
           rhs[3 * c + r] -= fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, A[3 * r + 2] * u2));
       }
     }
-    solve3x6(S, rhs);
+    float S[9];
+    nb_block(K, Et, 0, 0, 0, S);
+    solve3xn<kGsCases>(S, rhs);
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) u[q * N + v] = rhs[q];
+    for (int q = 0; q < 3 * kGsCases; ++q) u[(q0 + q) * N + v] = rhs[q];
   }
 }
 
@@ -229,6 +238,33 @@ __global__ void __launch_bounds__(128) k_fine_true_residual(const __grid_constan
     }
   }
   block_sum_store<kCases + kPlanes>(red, part);
+}
+
+// First Chebyshev step from x = 0: out_v = c0 S_v^-1 (b_v - bmean), S_v the diagonal
+// block (the Gauss-Seidel diagonal solve of Eq. 16).
+__global__ void __launch_bounds__(256) k_fine_jacobi_start(const __grid_constant__ KeParam K,
+                                                           const float* __restrict__ E,
+                                                           const float* __restrict__ b,
+                                                           const double* __restrict__ bmean,
+                                                           float* __restrict__ out, int n, float c0) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
+              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    float S[9];
+    nb_block(K, Et, 0, 0, 0, S);
+    float rhs[kPlanes];
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q)
+      rhs[q] = __ldg(b + q * N + v) - (bmean ? static_cast<float>(bmean[q]) : 0.f);
+    solve3x6(S, rhs);
+#pragma unroll
+    for (int q = 0; q < kPlanes; ++q) out[q * N + v] = c0 * rhs[q];
+  }
 }
 
 // Level-0 stencil written out (used only when the finest level is also the coarsest and
@@ -364,6 +400,12 @@ cudaError_t launch_simp(const float* rho_in, float* rho_out, float* E, size_t N,
   return cudaGetLastError();
 }
 
+cudaError_t launch_fine_jacobi_start(const homo_ctx* c, const float* b, const double* bmean, float* out,
+                                     float c0) {
+  k_fine_jacobi_start<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->ke, c->E, b, bmean, out, c->n, c0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fine_stencil(const homo_ctx* c, const Level& L0) {
   k_fine_stencil<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->ke, c->E, c->n, L0.colour_blocked, L0.st);
   return cudaGetLastError();
@@ -380,19 +422,22 @@ cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, dou
 }
 
 cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float* u,
-                                 const float* ulo, float* out, double* part, int* grid_out) {
+                                 const float* ulo, float* out, double* part, int* grid_out,
+                                 const double* bmean) {
   if (ulo) {
     const int g = grid_for(c->N, 128);
     if (grid_out) *grid_out = g;
     k_fine_true_residual<<<g, 128, 0, c->stream>>>(c->ke, c->E, u, ulo, b, out, c->n, part);
     return cudaGetLastError();
   }
-  return launch_fine_tiled(c, 3, u, b, out, nullptr, grid_out);
+  return launch_fine_tiled(c, 3, u, b, out, nullptr, grid_out, bmean);
 }
 
-cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first) {
+cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first,
+                           const double* fmean) {
   const size_t h = static_cast<size_t>(c->n / 2);
-  k_fine_gs<<<grid_for(h * h * h, 256), 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour, first);
+  const dim3 grid(grid_for(h * h * h, 256), kCases / kGsCases);
+  k_fine_gs<<<grid, 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour, first, fmean);
   return cudaGetLastError();
 }
 

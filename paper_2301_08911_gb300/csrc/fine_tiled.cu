@@ -50,6 +50,28 @@ __device__ __forceinline__ void tile_block(const KeParam& K, const float (&Et)[8
   }
 }
 
+// Solve the SPD 3x3 system S y = b for the 6 cases in place (LDL^T, FP32).
+__device__ __forceinline__ void solve3x6t(const float (&S)[9], float (&b)[18]) {
+  const float d0 = S[0];
+  const float l10 = S[3] / d0, l20 = S[6] / d0;
+  const float d1 = S[4] - l10 * S[1];
+  const float l21 = (S[7] - l20 * S[1]) / d1;
+  const float d2 = S[8] - l20 * S[2] - l21 * (S[5] - l10 * S[2]);
+  const float i0 = 1.f / d0, i1 = 1.f / d1, i2 = 1.f / d2;
+#pragma unroll
+  for (int c = 0; c < kCases; ++c) {
+    float y0 = b[3 * c], y1 = b[3 * c + 1], y2 = b[3 * c + 2];
+    y1 -= l10 * y0;
+    y2 -= l20 * y0 + l21 * y1;
+    const float x2 = y2 * i2;
+    const float x1 = y1 * i1 - l21 * x2;
+    const float x0 = y0 * i0 - l10 * x1 - l20 * x2;
+    b[3 * c] = x0;
+    b[3 * c + 1] = x1;
+    b[3 * c + 2] = x2;
+  }
+}
+
 // Per-thread load sites (fixed for every plane): halo site tid and, if it exists,
 // tid + 256, as in-plane offsets gy*n + gx; same for the moduli tile.
 struct Sites {
@@ -107,18 +129,30 @@ __device__ __forceinline__ void issue_e_plane(const float* __restrict__ E, size_
 
 // MODE 1: out = K u in difference form (sum_d A_d (u_(v+d) - u_v)) with partials of the
 //         dots (u_c, out_c) and the 18 plane sums of out (the CG product);
+// MODE 2: out = b - K (u + ulo) in difference form, each neighbour difference formed from
+//         the high and the low parts, (u_(v+d) - u_v) + (ulo_(v+d) - ulo_v), with partials of
+//         ||out_c||^2 and the 18 plane sums of out (the true residual of a double-float
+//         displacement, in FP32). The high difference is exact or within 2 ulp of the
+//         difference itself, so every term carries FP32 relative accuracy and the residual
+//         is accurate to ~1e-7 of sum_d |A_d| |u_(v+d) - u_v|; the low parts ride in a
+//         second bank of plane slots;
 // MODE 3: out = b - K u (the V-cycle residual).
+// MODE 4: out = u + c0 S^-1 (b - K u), S the 3x3 diagonal block (first Chebyshev step);
+// MODE 5: out = u + c0 (u - out) + c1 S^-1 (b - K u): a later Chebyshev step, the previous
+//         iterate read from out and replaced in place;
+// MODE 6: out = (1 + c0) u + c1 S^-1 (b - K u): the same step when the previous iterate is 0.
+// b is reduced by bmean (plane means) when bmean is non-null (modes 3-5).
 template <int MODE>
-__global__ void __launch_bounds__(kTiledThreads, 2) k_fine_tiled(const __grid_constant__ KeParam K,
-                                                                 const float* __restrict__ E,
-                                                                 const float* __restrict__ u,
-                                                                 const float* __restrict__ b,
-                                                                 float* __restrict__ out, int n,
-                                                                 int zchunk,
-                                                                 double* __restrict__ part) {
+__global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
+    k_fine_tiled(const __grid_constant__ KeParam K, const float* __restrict__ E,
+                 const float* __restrict__ u, const float* __restrict__ ulo,
+                 const float* __restrict__ b, float* out, int n, int zchunk,
+                 double* __restrict__ part, const double* __restrict__ bmean, float c0, float c1) {
+  constexpr bool kLo = MODE == 2;
   extern __shared__ float sm[];
   float* su = sm;                                   // kUSlots x 18 x PLANE
   float* se = sm + kUSlots * kUPlaneFloats;         // kESlots x EPLANE
+  float* sl = se + kESlots * EPLANE;                // low parts (MODE 2): kUSlots x 18 x PLANE
   const size_t N = static_cast<size_t>(n) * n * n;
   const size_t nn = static_cast<size_t>(n) * n;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -136,6 +170,7 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_fine_tiled(const __grid_co
   for (int p = -1; p <= 1; ++p) {
     const int zp = wrapi(z0 + p, n);
     issue_u_plane(u, N, zp * nn, s, su + ((z0 + p + kUSlots) & 3) * kUPlaneFloats);
+    if (kLo) issue_u_plane(ulo, N, zp * nn, s, sl + ((z0 + p + kUSlots) & 3) * kUPlaneFloats);
   }
   for (int p = -1; p <= 0; ++p) {
     const int zp = wrapi(z0 + p, n);
@@ -147,14 +182,15 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_fine_tiled(const __grid_co
     // prefetch u plane z+2 and modulus plane z+1 (their slots were released at the end
     // of the previous step)
     issue_u_plane(u, N, static_cast<size_t>(wrapi(z + 2, n)) * nn, s, su + ((z + 2) & 3) * kUPlaneFloats);
+    if (kLo)
+      issue_u_plane(ulo, N, static_cast<size_t>(wrapi(z + 2, n)) * nn, s, sl + ((z + 2) & 3) * kUPlaneFloats);
     issue_e_plane(E, static_cast<size_t>(wrapi(z + 1, n)) * nn, s, se + ((z + 1) % kESlots) * EPLANE);
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
     if (live) {
-      const float* pm = su + ((z + 3) & 3) * kUPlaneFloats;   // plane z-1
-      const float* p0 = su + (z & 3) * kUPlaneFloats;         // plane z
-      const float* pp = su + ((z + 1) & 3) * kUPlaneFloats;   // plane z+1
+      const int sm1 = ((z + 3) & 3) * kUPlaneFloats, s0 = (z & 3) * kUPlaneFloats,
+                sp1 = ((z + 1) & 3) * kUPlaneFloats;               // planes z-1, z, z+1
       const float* em = se + ((z + 2) % kESlots) * EPLANE;     // elements with origin z-1
       const float* e0 = se + (z % kESlots) * EPLANE;           // elements with origin z
       float Et[8];
@@ -162,28 +198,40 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_fine_tiled(const __grid_co
       for (int t = 0; t < 8; ++t)
         Et[t] = ((t >> 2) ? e0 : em)[(ty + ((t >> 1) & 1)) * EX + tx + (t & 1)];
       const int cidx = (ty + 1) * HX + tx + 1;
-      float own[kPlanes];
-      if (MODE == 1) {
+      constexpr bool kDiff = MODE == 1 || MODE == 2;
+      float own[kPlanes], ownlo[kLo ? kPlanes : 1];
+      if (kDiff) {
 #pragma unroll
-        for (int q = 0; q < kPlanes; ++q) own[q] = p0[q * PLANE + cidx];
+        for (int q = 0; q < kPlanes; ++q) own[q] = su[s0 + q * PLANE + cidx];
       }
+      if (kLo) {
+#pragma unroll
+        for (int q = 0; q < kPlanes; ++q) ownlo[kLo ? q : 0] = sl[s0 + q * PLANE + cidx];
+      }
+      constexpr bool kCheb = MODE == 4 || MODE == 5 || MODE == 6;
       float acc[kPlanes];
 #pragma unroll
       for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
+      float S[9];
 #pragma unroll
       for (int d = 0; d < 27; ++d) {
-        if (MODE == 1 && d == 13) continue;
+        if (kDiff && d == 13) continue;
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
         float A[9];
         tile_block(K, Et, dx, dy, dz, A);
-        const float* p = (dz < 0 ? pm : (dz == 0 ? p0 : pp)) + cidx + dy * HX + dx;
+        if (kCheb && d == 13) {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) S[q] = A[q];
+        }
+        const int off = (dz < 0 ? sm1 : (dz == 0 ? s0 : sp1)) + cidx + dy * HX + dx;
 #pragma unroll
         for (int c = 0; c < kCases; ++c) {
           float uu[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            uu[k] = p[(3 * c + k) * PLANE];
-            if (MODE == 1) uu[k] -= own[3 * c + k];
+            uu[k] = su[off + (3 * c + k) * PLANE];
+            if (kDiff) uu[k] -= own[3 * c + k];
+            if (kLo) uu[k] += sl[off + (3 * c + k) * PLANE] - ownlo[kLo ? 3 * c + k : 0];
           }
 #pragma unroll
           for (int r = 0; r < 3; ++r)
@@ -191,21 +239,37 @@ __global__ void __launch_bounds__(kTiledThreads, 2) k_fine_tiled(const __grid_co
         }
       }
       const size_t v = static_cast<size_t>(z) * nn + static_cast<size_t>(y) * n + x;
+      if (kCheb) {
+        // residual, block-diagonal solve, Chebyshev update
 #pragma unroll
-      for (int q = 0; q < kPlanes; ++q) {
-        const size_t o = q * N + v;
-        float val = acc[q];
-        if (MODE == 3) val = __ldg(b + o) - val;
-        out[o] = val;
-        if (MODE == 1) {
-          red[q / 3] = fmaf(own[q], val, red[q / 3]);
-          red[kCases + q] += val;
+        for (int q = 0; q < kPlanes; ++q)
+          acc[q] = (__ldg(b + q * N + v) - (bmean ? static_cast<float>(bmean[q]) : 0.f)) - acc[q];
+        solve3x6t(S, acc);
+#pragma unroll
+        for (int q = 0; q < kPlanes; ++q) {
+          const size_t o = q * N + v;
+          const float uc = su[s0 + q * PLANE + cidx];
+          if (MODE == 4) out[o] = fmaf(c0, acc[q], uc);
+          else if (MODE == 5) out[o] = fmaf(c1, acc[q], fmaf(c0, uc - out[o], uc));
+          else out[o] = fmaf(c1, acc[q], fmaf(c0, uc, uc));
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kPlanes; ++q) {
+          const size_t o = q * N + v;
+          float val = acc[q];
+          if (MODE == 3) val = (__ldg(b + o) - (bmean ? static_cast<float>(bmean[q]) : 0.f)) - val;
+          if (MODE == 2) val = __ldg(b + o) - val;
+          out[o] = val;
+          if (MODE == 1) red[q / 3] = fmaf(own[q], val, red[q / 3]);
+          if (MODE == 2) red[q / 3] = fmaf(val, val, red[q / 3]);
+          if (kDiff) red[kCases + q] += val;
         }
       }
     }
     __syncthreads();
   }
-  if (MODE == 1 && part != nullptr) {
+  if ((MODE == 1 || MODE == 2) && part != nullptr) {
     // block_sum_store writes row blockIdx.x; shift the base to the flattened 3-D index
     const size_t flat = (static_cast<size_t>(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     block_sum_store<kCases + kPlanes>(red, part + (flat - blockIdx.x) * (kCases + kPlanes));
@@ -222,31 +286,47 @@ int tiled_zchunk(int n) {
 
 }  // namespace
 
-size_t tiled_smem_bytes() { return sizeof(float) * (kUSlots * kUPlaneFloats + kESlots * EPLANE); }
+size_t tiled_smem_bytes(int mode) {
+  return sizeof(float) * (kUSlots * kUPlaneFloats * (mode == 2 ? 2 : 1) + kESlots * EPLANE);
+}
 
 int tiled_grid_blocks(int n) {
   const int zc = tiled_zchunk(n);
   return ((n + TX - 1) / TX) * ((n + TY - 1) / TY) * ((n + zc - 1) / zc);
 }
 
+namespace {
+template <int MODE>
+cudaError_t run_tiled(const homo_ctx* c, dim3 grid, int zc, const float* u, const float* ulo, const float* b,
+                      float* out, double* part, const double* bmean, float c0, float c1) {
+  const size_t shm = tiled_smem_bytes(MODE);
+  cudaError_t e = cudaFuncSetAttribute(k_fine_tiled<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(shm));
+  if (e != cudaSuccess) return e;
+  k_fine_tiled<MODE><<<grid, kTiledThreads, shm, c->stream>>>(c->ke, c->E, u, ulo, b, out, c->n, zc, part,
+                                                              bmean, c0, c1);
+  return cudaGetLastError();
+}
+}  // namespace
+
 cudaError_t launch_fine_tiled(const homo_ctx* c, int mode, const float* u, const float* b, float* out,
-                              double* part, int* grid_out) {
+                              double* part, int* grid_out, const double* bmean, float c0, float c1,
+                              const float* ulo) {
   const int n = c->n;
   const int zc = tiled_zchunk(n);
   dim3 grid((n + TX - 1) / TX, (n + TY - 1) / TY, (n + zc - 1) / zc);
   if (grid_out) *grid_out = static_cast<int>(grid.x * grid.y * grid.z);
-  const size_t shm = tiled_smem_bytes();
-  cudaError_t e;
-  if (mode == 1) {
-    e = cudaFuncSetAttribute(k_fine_tiled<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm));
-    if (e != cudaSuccess) return e;
-    k_fine_tiled<1><<<grid, kTiledThreads, shm, c->stream>>>(c->ke, c->E, u, nullptr, out, n, zc, part);
-  } else {
-    e = cudaFuncSetAttribute(k_fine_tiled<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm));
-    if (e != cudaSuccess) return e;
-    k_fine_tiled<3><<<grid, kTiledThreads, shm, c->stream>>>(c->ke, c->E, u, b, out, n, zc, nullptr);
+  switch (mode) {
+    case 1: return run_tiled<1>(c, grid, zc, u, nullptr, nullptr, out, part, nullptr, 0.f, 0.f);
+    case 2:
+      if (!ulo) return cudaErrorInvalidValue;
+      return run_tiled<2>(c, grid, zc, u, ulo, b, out, part, nullptr, 0.f, 0.f);
+    case 3: return run_tiled<3>(c, grid, zc, u, nullptr, b, out, nullptr, bmean, 0.f, 0.f);
+    case 4: return run_tiled<4>(c, grid, zc, u, nullptr, b, out, nullptr, bmean, c0, c1);
+    case 5: return run_tiled<5>(c, grid, zc, u, nullptr, b, out, nullptr, bmean, c0, c1);
+    case 6: return run_tiled<6>(c, grid, zc, u, nullptr, b, out, nullptr, bmean, c0, c1);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace homo

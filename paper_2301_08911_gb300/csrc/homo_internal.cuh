@@ -79,7 +79,8 @@ enum Slot : int {
   S_ACTIVE = 96,   // 1.0 while case c iterates  [6]
   S_CH = 102,      // C^H sums                   [21]
   S_OC = 128,      // OC scratch                 [64]
-  S_COUNT = 192
+  S_RMEAN = 192,   // plane means of r, subtracted by every consumer of r [18]
+  S_COUNT = 210
 };
 
 struct homo_ctx_impl;
@@ -100,6 +101,8 @@ struct homo_ctx {
   float* E = nullptr;        // element moduli, N
   float* u = nullptr;        // displacement, 18N (high part)
   float* ulo = nullptr;      // displacement low part (u = u + ulo exactly), 18N
+  float* ecyc = nullptr;     // correction accumulated during one CG cycle, 18N (high part)
+  float* ecyclo = nullptr;   // its low part: the correction is kept in double-float
   float* f = nullptr;        // loads, 18N
   float* r = nullptr;        // CG residual, 18N
   float* z = nullptr;        // preconditioned residual, 18N
@@ -136,6 +139,9 @@ struct homo_ctx {
 
   // relative residual of the 6 cases after every CG iteration of the last solve
   std::vector<double> history;
+
+  // Chebyshev smoother: upper end of the spectrum of D^-1 K per smoothed level
+  double lam[homo::kMaxLevels] = {};
 };
 
 namespace homo {
@@ -153,16 +159,38 @@ cudaError_t launch_loads(const homo_ctx* c, float* f);
 // dots (u_c, out_c) and the 18 plane sums of out (24 doubles per block; *grid_out blocks).
 cudaError_t launch_fine_apply(const homo_ctx* c, const float* u, float* out, double* part,
                               int* grid_out);
-// tiled finest-level stencil (fine_tiled.cu): mode 1 = launch_fine_apply, mode 3 = b - K u
+// tiled finest-level stencil (fine_tiled.cu): mode 1 = launch_fine_apply; 2 = b - K (u + ulo)
+// in difference form from both parts, with norms (FP32 true residual); 3 = (b - bmean) - K u;
+// 4 = u + c0 S^-1 (b - bmean - K u); 5 = u + c0 (u - out) + c1 S^-1 (b - bmean - K u), in
+// place on out; 6 = (1 + c0) u + c1 S^-1 (b - bmean - K u) (Chebyshev steps)
 cudaError_t launch_fine_tiled(const homo_ctx* c, int mode, const float* u, const float* b, float* out,
-                              double* part, int* grid_out);
-size_t tiled_smem_bytes();
+                              double* part, int* grid_out, const double* bmean = nullptr,
+                              float c0 = 0.f, float c1 = 0.f, const float* ulo = nullptr);
+// out = c0 S^-1 (b - bmean) pointwise on level 0 (first Chebyshev step from zero)
+cudaError_t launch_fine_jacobi_start(const homo_ctx* c, const float* b, const double* bmean, float* out,
+                                     float c0);
+// coarse Chebyshev step with the stored stencil: x_in == null means x_in = 0;
+// mode 0: out = x_in + c0 S^-1 (b - K x_in); mode 1: out = x_in + c0 (x_in - out) + c1 S^-1 (b - K x_in);
+// mode 3: out = (1 + c0) x_in + c1 S^-1 (b - K x_in)
+cudaError_t launch_coarse_cheb(const Level& L, const float* b, const float* x_in, float* out, int mode,
+                               float c0, float c1, cudaStream_t s);
+// y = S^-1 K x on a stored-stencil level (power iteration for the Chebyshev interval)
+cudaError_t launch_coarse_dinvk(const Level& L, const float* x, float* y, cudaStream_t s);
+cudaError_t launch_fill_hash(float* x, size_t count, unsigned seed, cudaStream_t s);
+// largest eigenvalue of blockdiag(K0)^-1 K0 (host arithmetic)
+double element_jacobi_bound(const KeParam& ke);
+size_t tiled_smem_bytes(int mode);
 int tiled_grid_blocks(int n);
-// out = b - K (u + ulo) in difference form (accurate true residual); partials of ||out_c||^2.
+// ulo != null: out = b - K (u + ulo) in double-float (accurate true residual) with
+// partials of ||out_c||^2 and plane sums; ulo == null: out = (b - bmean) - K u (bmean: 18
+// plane means or null).
 cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float* u,
-                                 const float* ulo, float* out, double* part, int* grid_out);
-// first != 0: first sweep from u = 0, colours 0..7 (u need not be cleared)
-cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first);
+                                 const float* ulo, float* out, double* part, int* grid_out,
+                                 const double* bmean);
+// first != 0: first sweep from u = 0, colours 0..7 (u need not be cleared); fmean: plane
+// means subtracted from f, or null
+cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first,
+                           const double* fmean);
 cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, float* sens,
                              double* part, int* grid_out);
 
@@ -188,15 +216,19 @@ cudaError_t launch_sum_partials(const double* part, int nblk, int nv, double* ou
                                 cudaStream_t s);
 cudaError_t launch_dot6(const float* a, const float* b, size_t N, double* part, int* grid_out,
                         cudaStream_t s);
-cudaError_t launch_dot6_zsum(const float* r, const float* z, size_t N, double* part,
-                             int* grid_out, cudaStream_t s);
+// (r - rmean, z) per case and plane sums of z; rmean: 18 doubles or null
+cudaError_t launch_dot6_zsum(const float* r, const float* z, size_t N, const double* rmean,
+                             double* part, int* grid_out, cudaStream_t s);
 cudaError_t launch_cg_alpha(double* scal, cudaStream_t s);
 cudaError_t launch_cg_beta(double* scal, int first, cudaStream_t s);
-cudaError_t launch_cg_active(double* scal, double tol, int centre, size_t N, cudaStream_t s);
-cudaError_t launch_center(float* r, const double* scal, size_t N, cudaStream_t s);
-cudaError_t launch_cg_update_xr(float* u, float* ulo, float* r, const float* p, const float* q,
+// centred norms and plane means of r from its raw sums, active flags
+cudaError_t launch_cg_active(double* scal, double tol, size_t N, cudaStream_t s);
+// e += alpha p, r -= alpha (q - mean q), partials of ||r||^2 and plane sums of r
+cudaError_t launch_cg_update_er(float* e, float* elo, float* r, const float* p, const float* q,
                                 const double* scal, size_t N, double* part, int* grid_out,
                                 cudaStream_t s);
+// (u, ulo) += e in double-float, e = 0
+cudaError_t launch_fold(float* u, float* ulo, float* e, float* elo, size_t n, cudaStream_t s);
 cudaError_t launch_cg_update_p(float* p, const float* z, const double* scal, size_t N,
                                cudaStream_t s);
 cudaError_t launch_split_set(float* hi, float* lo, const float* src, size_t n, cudaStream_t s);

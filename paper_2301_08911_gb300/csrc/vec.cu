@@ -41,19 +41,23 @@ __global__ void __launch_bounds__(256) k_dot6(const float* __restrict__ a,
   block_sum_store<kCases>(red, part);
 }
 
-// (r_c, z_c) for the 6 cases and the 18 plane sums of z (for removing the mean).
+// (r_c - mean r, z_c) for the 6 cases and the 18 plane sums of z (for removing its mean).
+// rmean: 18 plane means of r (doubles), or null.
 __global__ void __launch_bounds__(256) k_dot6_zsum(const float* __restrict__ r,
                                                    const float* __restrict__ z, size_t N,
+                                                   const double* __restrict__ rmean,
                                                    double* __restrict__ part) {
-  float red[kCases + kPlanes];
+  float red[kCases + kPlanes], rm[kPlanes];
 #pragma unroll
   for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
+#pragma unroll
+  for (int q = 0; q < kPlanes; ++q) rm[q] = rmean ? static_cast<float>(rmean[q]) : 0.f;
   for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
        v += static_cast<size_t>(gridDim.x) * blockDim.x) {
 #pragma unroll
     for (int q = 0; q < kPlanes; ++q) {
       const float zz = __ldg(z + q * N + v);
-      red[q / 3] = fmaf(__ldg(r + q * N + v), zz, red[q / 3]);
+      red[q / 3] = fmaf(__ldg(r + q * N + v) - rm[q], zz, red[q / 3]);
       red[kCases + q] += zz;
     }
   }
@@ -80,38 +84,32 @@ __global__ void k_cg_beta(double* __restrict__ s, int first) {
   s[S_RZ_OLD + c] = rz;
 }
 
-// Case c keeps iterating while ||r_c||^2 > tol^2 ||f_c||^2. With centre != 0 the residual
-// has just had its plane means removed: ||r_c||^2 loses N * mean^2 per plane.
-__global__ void k_cg_active(double* __restrict__ s, double tol2, int centre, double N) {
+// The stored residual keeps the plane means it had when it was last recomputed (the
+// rigid translations, outside the range of K); every consumer subtracts them. This
+// kernel turns the raw sums into the centred norms ||r_c - mean||^2 = sum r^2 - sum^2/N
+// and the plane means, and marks case c active while ||r_c||^2 > tol^2 ||f_c||^2.
+__global__ void k_cg_active(double* __restrict__ s, double tol2, double N) {
   const int c = threadIdx.x;
   if (c >= kCases) return;
   double rr = s[S_RR + c];
-  if (centre) {
-    for (int k = 0; k < 3; ++k) rr -= s[S_RSUM + 3 * c + k] * s[S_RSUM + 3 * c + k] / N;
-    rr = fmax(rr, 0.0);
-    s[S_RR + c] = rr;
+  for (int k = 0; k < 3; ++k) {
+    const double sum = s[S_RSUM + 3 * c + k];
+    rr -= sum * sum / N;
+    s[S_RMEAN + 3 * c + k] = sum / N;
   }
+  rr = fmax(rr, 0.0);
+  s[S_RR + c] = rr;
   const double ff = s[S_FF + c];
   s[S_ACTIVE + c] = (ff > 0.0 && rr > tol2 * ff) ? 1.0 : 0.0;
 }
 
-// r -= mean(r) per plane (the rigid-translation component, which K cannot produce).
-__global__ void __launch_bounds__(256) k_center(float* __restrict__ r, const double* __restrict__ s,
-                                                size_t N) {
-  float m[kPlanes];
-#pragma unroll
-  for (int k = 0; k < kPlanes; ++k) m[k] = static_cast<float>(s[S_RSUM + k] / static_cast<double>(N));
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
-#pragma unroll
-    for (int k = 0; k < kPlanes; ++k) r[static_cast<size_t>(k) * N + v] -= m[k];
-  }
-}
-
-// u (+ ulo) += alpha p in double-float arithmetic (error-free transformations with
-// non-contracted operations), r -= alpha (q - mean q), partial sums of ||r_c||^2 and of
-// the 18 plane sums of r.
-__global__ void __launch_bounds__(256) k_cg_update_xr(float* __restrict__ u, float* __restrict__ ulo,
+// e += alpha p, e kept in double-float (e + elo): the product is split exactly (its
+// rounding error recovered with an FMA) and both parts are added with error-free
+// transformations, so the correction carries no FP32 rounding noise; K applied to such
+// noise would be amplified by the operator's spread of eigenvalues and leave the true
+// residual far above the recursive one. r -= alpha (q - mean q) in FP32. Partial sums of
+// ||r_c||^2 and of the 18 plane sums of r.
+__global__ void __launch_bounds__(256) k_cg_update_er(float* __restrict__ e, float* __restrict__ elo,
                                                       float* __restrict__ r,
                                                       const float* __restrict__ p,
                                                       const float* __restrict__ q,
@@ -133,18 +131,18 @@ __global__ void __launch_bounds__(256) k_cg_update_xr(float* __restrict__ u, flo
       const size_t o = static_cast<size_t>(k) * N + v;
       float rv = r[o];
       if (a[c] != 0.f) {
-        const float pv = p[o];
-        const float pa = __fmul_rn(a[c], pv);
-        const float pe = fmaf(a[c], pv, -pa);            // exact product error
-        const float hi = u[o];
-        const float sm = __fadd_rn(hi, pa);              // TwoSum(hi, pa)
+        const float pv = __ldg(p + o);
+        const float pr = __fmul_rn(a[c], pv);              // TwoProd: pr + pe = a p exactly
+        const float pe = fmaf(a[c], pv, -pr);
+        const float hi = e[o];
+        const float sm = __fadd_rn(hi, pr);                // TwoSum(hi, pr)
         const float bb = __fadd_rn(sm, -hi);
-        const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(sm, -bb)), __fadd_rn(pa, -bb));
-        const float lo = __fadd_rn(__fadd_rn(ulo[o], e), pe);
-        const float s2 = __fadd_rn(sm, lo);              // FastTwoSum renormalisation
-        u[o] = s2;
-        ulo[o] = __fadd_rn(lo, -__fadd_rn(s2, -sm));
-        rv = fmaf(-a[c], q[o] - qm[k], rv);
+        const float er = __fadd_rn(__fadd_rn(hi, -__fadd_rn(sm, -bb)), __fadd_rn(pr, -bb));
+        const float lo = __fadd_rn(__fadd_rn(elo[o], pe), er);
+        const float s2 = __fadd_rn(sm, lo);                // FastTwoSum renormalisation
+        e[o] = s2;
+        elo[o] = __fadd_rn(lo, -__fadd_rn(s2, -sm));
+        rv = fmaf(-a[c], __ldg(q + o) - qm[k], rv);
         r[o] = rv;
       }
       red[c] = fmaf(rv, rv, red[c]);
@@ -152,6 +150,28 @@ __global__ void __launch_bounds__(256) k_cg_update_xr(float* __restrict__ u, flo
     }
   }
   block_sum_store<kCases + kPlanes>(red, part);
+}
+
+// (u + ulo) += (e + elo) in double-float arithmetic (error-free transformations with
+// non-contracted operations), then e = elo = 0. Closes a CG cycle.
+__global__ void __launch_bounds__(256) k_fold(float* __restrict__ u, float* __restrict__ ulo,
+                                              float* __restrict__ e, float* __restrict__ elo,
+                                              size_t n) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const float d = e[i], dlo = elo[i];
+    if (d == 0.f && dlo == 0.f) continue;
+    const float hi = u[i];
+    const float sm = __fadd_rn(hi, d);                   // TwoSum(hi, d)
+    const float bb = __fadd_rn(sm, -hi);
+    const float er = __fadd_rn(__fadd_rn(hi, -__fadd_rn(sm, -bb)), __fadd_rn(d, -bb));
+    const float lo = __fadd_rn(__fadd_rn(ulo[i], dlo), er);
+    const float s2 = __fadd_rn(sm, lo);                  // FastTwoSum renormalisation
+    u[i] = s2;
+    ulo[i] = __fadd_rn(lo, -__fadd_rn(s2, -sm));
+    e[i] = 0.f;
+    elo[i] = 0.f;
+  }
 }
 
 // p = (z - mean(z)) + beta p per plane.
@@ -398,11 +418,11 @@ cudaError_t launch_dot6(const float* a, const float* b, size_t N, double* part, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_dot6_zsum(const float* r, const float* z, size_t N, double* part,
-                             int* grid_out, cudaStream_t s) {
+cudaError_t launch_dot6_zsum(const float* r, const float* z, size_t N, const double* rmean,
+                             double* part, int* grid_out, cudaStream_t s) {
   const int g = grid_for(N, 256);
   *grid_out = g;
-  k_dot6_zsum<<<g, 256, 0, s>>>(r, z, N, part);
+  k_dot6_zsum<<<g, 256, 0, s>>>(r, z, N, rmean, part);
   return cudaGetLastError();
 }
 
@@ -416,22 +436,22 @@ cudaError_t launch_cg_beta(double* scal, int first, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_active(double* scal, double tol, int centre, size_t N, cudaStream_t s) {
-  k_cg_active<<<1, 32, 0, s>>>(scal, tol * tol, centre, static_cast<double>(N));
+cudaError_t launch_cg_active(double* scal, double tol, size_t N, cudaStream_t s) {
+  k_cg_active<<<1, 32, 0, s>>>(scal, tol * tol, static_cast<double>(N));
   return cudaGetLastError();
 }
 
-cudaError_t launch_center(float* r, const double* scal, size_t N, cudaStream_t s) {
-  k_center<<<grid_for(N, 256), 256, 0, s>>>(r, scal, N);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_cg_update_xr(float* u, float* ulo, float* r, const float* p, const float* q,
+cudaError_t launch_cg_update_er(float* e, float* elo, float* r, const float* p, const float* q,
                                 const double* scal, size_t N, double* part, int* grid_out,
                                 cudaStream_t s) {
   const int g = grid_for(N, 256);
   *grid_out = g;
-  k_cg_update_xr<<<g, 256, 0, s>>>(u, ulo, r, p, q, scal, N, part);
+  k_cg_update_er<<<g, 256, 0, s>>>(e, elo, r, p, q, scal, N, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold(float* u, float* ulo, float* e, float* elo, size_t n, cudaStream_t s) {
+  k_fold<<<grid_for(n, 256), 256, 0, s>>>(u, ulo, e, elo, n);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,19 @@ def test_element_matrix_matches_oracle_quadrature(lib):
         assert np.abs(K - Ko).max() < 4e-7 * np.abs(Ko).max()
 
 
+@pytest.mark.parametrize("nu", [0.3, 0.2, 0.45])
+def test_element_jacobi_bound_matches_dense_eigensolver(lib, nu):
+    """The Chebyshev interval end on the finest level: max eig of blockdiag(K0)^-1 K0."""
+    K = oracle.ke_hex8(1.0, nu, 1.0)
+    D = np.zeros_like(K)
+    for j in range(8):
+        D[3 * j:3 * j + 3, 3 * j:3 * j + 3] = K[3 * j:3 * j + 3, 3 * j:3 * j + 3]
+    want = np.linalg.eigvals(np.linalg.solve(D, K)).real.max()
+    got = ctypes.c_double()
+    assert lib.homo_element_jacobi_bound(nu, ctypes.byref(got)) == binding.HOMO_OK
+    assert abs(got.value - want) < 1e-6 * want
+
+
 @pytest.mark.parametrize("kind", ["bulk", "shear", "poisson", "logpoisson"])
 def test_objectives_match_oracle(lib, kind):
     rng = np.random.default_rng(3)

@@ -141,9 +141,9 @@ def test_gauss_seidel_sweep_matches_oracle(B, level, reverse):
     assert rel(dofs(host(ut).reshape(18, -1), nl), ref) < 2e-6
 
 
-def test_vcycle_is_symmetric_positive(B):
-    n = 16
-    hom = make(B, n)
+@pytest.mark.parametrize("smoother,n", [("gs8", 16), ("chebyshev", 16), ("chebyshev", 24)])
+def test_vcycle_is_symmetric_positive(B, smoother, n):
+    hom = make(B, n, smoother=smoother)
     hom.set_density(cuda(smoothed_threshold_density(n, 0.3, 1)))
     x = mean_free(uniform_field(18 * n ** 3, 600, -1, 1).reshape(18, -1).astype(np.float64))
     y = mean_free(uniform_field(18 * n ** 3, 601, -1, 1).reshape(18, -1).astype(np.float64))
@@ -162,8 +162,8 @@ def test_vcycle_is_symmetric_positive(B):
 _CASES = {}
 
 
-def _solved(B, n, kind):
-    key = (n, kind)
+def _solved(B, n, kind, smoother="gs8"):
+    key = (n, kind, smoother)
     if key in _CASES:
         return _CASES[key]
     if kind == "c1":
@@ -172,7 +172,7 @@ def _solved(B, n, kind):
         rho = uniform_density(n, 700 + n, 0.05, 1.0)
     rho_t = oracle.cone_filter(rho, n, 2.0).astype(np.float32)
     ref = oracle.homogenize(rho_t.astype(np.float64), n)
-    hom = make(B, n)
+    hom = make(B, n, smoother=smoother)
     hom.set_density(cuda(rho_t))
     # well below the configs' 1e-6 so that the comparison measures the kernels' FP32
     # arithmetic, not the stopping tolerance (the sensitivity error is first order in it)
@@ -181,9 +181,11 @@ def _solved(B, n, kind):
     return _CASES[key]
 
 
-@pytest.mark.parametrize("n,kind", [(16, "c1"), (20, "uniform"), (24, "uniform"), (12, "uniform")])
-def test_CH_matches_oracle(B, n, kind):
-    hom, rho_t, ref, its, relres = _solved(B, n, kind)
+@pytest.mark.parametrize("n,kind,smoother", [(16, "c1", "gs8"), (20, "uniform", "gs8"), (24, "uniform", "gs8"),
+                                             (12, "uniform", "gs8"), (16, "c1", "chebyshev"),
+                                             (24, "uniform", "chebyshev")])
+def test_CH_matches_oracle(B, n, kind, smoother):
+    hom, rho_t, ref, its, relres = _solved(B, n, kind, smoother)
     assert max(relres) <= 1e-9
     assert hom.residual_history().shape[1] == 6
     C = hom.CH()
@@ -225,6 +227,52 @@ def test_single_level_direct_solve(B, n):
     hom.set_density(cuda(rho_t))
     _, relres, _ = hom.solve_cases(1e-7, 50, warm_start=False)
     assert rel(hom.CH(), ref["C"]) < 1e-6
+
+
+# ---------------------------------------------------------------- true residual evaluations
+def _oracle_relres(n, rho_t, u18):
+    """||f - K u|| / ||f|| per case in FP64, rigid translations removed (voxel units)."""
+    Ke = oracle.ke_hex8(1.0, 0.3, 1.0)
+    Ee = oracle.simp_modulus(rho_t.astype(np.float64))
+    K = oracle.assemble_K(n, Ee, Ke)
+    f = oracle.macro_strain_loads(n, Ee, Ke, oracle.macro_strain_displacements(1.0))
+    r = f - (K @ dofs(u18, n).T).T
+    r = mean_free(planes(r, n))
+    fp = planes(f, n)
+    return np.array([np.linalg.norm(r[3 * i:3 * i + 3]) / np.linalg.norm(fp[3 * i:3 * i + 3])
+                     for i in range(6)])
+
+
+@pytest.mark.parametrize("n", [16, 20])
+def test_residual_evaluations_match_oracle(B, n):
+    """Both evaluations of f - K u against FP64 sparse algebra on a random field."""
+    rho_t = oracle.cone_filter(smoothed_threshold_density(n, 0.3, 3), n, 2.0).astype(np.float32)
+    u = (uniform_field(18 * n ** 3, 40 + n) - 0.5).astype(np.float32).reshape(18, -1) * n
+    hom = make(B, n)
+    hom.set_density(cuda(rho_t))
+    hom.set_displacement(cuda(u.ravel()))
+    want = _oracle_relres(n, rho_t, u.astype(np.float64))
+    for method in ("fp32", "double_float"):
+        got = hom.residual(method)
+        assert np.abs(got / want - 1).max() < 1e-5, (method, got, want)
+
+
+def test_fp32_residual_error_on_a_converged_solution(B):
+    """On a converged 64^3 solution the FP32 difference-form residual stays within 1e-6
+    of ||f|| of the double-float one (the size of error a start from it may carry), and a
+    solve at 1e-5, which starts from it, meets its tolerance in double-float arithmetic."""
+    n = 64
+    rho_t = oracle.cone_filter(smoothed_threshold_density(n, 0.3, 2), n, 2.0).astype(np.float32)
+    hom = make(B, n)
+    hom.set_density(cuda(rho_t))
+    _, relres, _ = hom.solve_cases(1e-9, 800, warm_start=False)
+    exact, fast = hom.residual("double_float"), hom.residual("fp32")
+    assert max(exact) <= 1e-9 * 1.0001
+    assert np.abs(fast - exact).max() < 1e-6, (fast, exact)
+    hom.set_density(cuda(rho_t * np.float32(0.98) + np.float32(0.01)))
+    _, relres, _ = hom.solve_cases(1e-5, 400, warm_start=True)
+    assert max(relres) <= 1e-5
+    assert max(hom.residual("double_float")) <= 1e-5 * 1.0001
 
 
 # ---------------------------------------------------------------- closed forms on the GPU
@@ -303,12 +351,13 @@ def test_oc_unattainable_volume_goes_to_bounds(B):
 
 
 # ---------------------------------------------------------------- whole iteration
-def test_full_iteration_matches_oracle_16(B):
+@pytest.mark.parametrize("smoother", ["gs8", "chebyshev"])
+def test_full_iteration_matches_oracle_16(B, smoother):
     """One bulk-modulus iteration at 16^3 on the blurred-noise cell at volume fraction 0.3."""
     n, V = 16, 0.3
     rho = smoothed_threshold_density(n, V, 1)
     ref = oracle.optimization_iteration(rho.astype(np.float64), n, V, "bulk")
-    hom = make(B, n)
+    hom = make(B, n, smoother=smoother)
     r = cuda(rho)
     rt = torch.empty_like(r)
     hom.filter(2.0, r, rt)
