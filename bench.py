@@ -50,8 +50,15 @@ def parse_args(argv=None):
     ap.add_argument("--sample-n", type=int, default=16, help="cell size of the oracle's CPU sample")
     ap.add_argument("--sweeps", type=int, default=0, help="smoothing sweeps before/after coarse correction (0 = library default)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
+                    help="mixed: coarse-level stencils of the preconditioner stored in BF16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--record-traffic", metavar="NCU_CSV",
+                    help="write profiles/traffic.json from an ncu --csv capture of "
+                         "dram__bytes_read.sum and dram__bytes_write.sum (one V-cycle's k_fine_gs "
+                         "launches at --n) and exit")
+    ap.add_argument("--traffic-command", default="", help="the capture command, stored beside the figure")
     return ap.parse_args(argv)
 
 
@@ -254,6 +261,10 @@ def config_dict(args):
             "density": f"seeded blurred-noise inclusions (seed {args.seed}), exactly vf solid",
             "l2": "inputs larger than L2 (18 planes x n^3 fp32 per field)",
             "parallelism": "replicas (one cell per GPU, no collective)",
+            "precision": ("FP32 storage and arithmetic; double-float displacement and CG correction"
+                          if args.precision == "fp32" else
+                          "FP32 arithmetic; coarse-level stencils stored in BF16 (symmetrised); "
+                          "double-float displacement and CG correction"),
             "smoother": (f"8-colour block Gauss-Seidel, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle"
                          if args.smoother == "gs8" else
                          f"Chebyshev(2)/block-Jacobi, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle")}
@@ -294,7 +305,8 @@ def run_ours(args, rank, world, local):
     n = args.n
     rho0 = smoothed_threshold_density(n, args.vf, args.seed + rank)
     stream = torch.cuda.current_stream(dev)
-    hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream, smoother=args.smoother)
+    hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream, smoother=args.smoother,
+                                 precision=args.precision)
     r = torch.from_numpy(rho0).to(dev)
     rt = torch.empty_like(r)
     s = torch.empty_like(r)
@@ -427,8 +439,40 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+def record_traffic(args) -> int:
+    """Average DRAM bytes per launch of the fine Gauss-Seidel pass from an ncu CSV (the
+    captured launches should be one V-cycle's 16 passes, first sweep included, which the
+    roofline's algorithmic bytes average over too)."""
+    import csv
+    rows = list(csv.reader(open(args.record_traffic)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ki, mi, vi, ui = h.index("Kernel Name"), h.index("Metric Name"), h.index("Metric Value"), h.index("Metric Unit")
+    idx = h.index("ID") if "ID" in h else None
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per = {}
+    for r in rows[hi + 1:]:
+        if len(r) <= vi or "k_fine_gs" not in r[ki]:
+            continue
+        if r[mi] in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            key = r[idx] if idx is not None else len(per)
+            per[key] = per.get(key, 0.0) + float(r[vi].replace(",", "")) * scale[r[ui]]
+    if not per:
+        raise SystemExit("no k_fine_gs DRAM rows in " + args.record_traffic)
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    d = json.load(open(path)) if os.path.exists(path) else {}
+    d["fine_gs"] = {"n": args.n, "launches": len(per), "dram_bytes_per_launch": sum(per.values()) / len(per),
+                    "source_hash": kernel_source_hash(), "command": args.traffic_command}
+    with open(path, "w") as fh:
+        json.dump(d, fh, indent=1)
+    print(json.dumps(d["fine_gs"]))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.record_traffic:
+        return record_traffic(args)
     rank, world, local = dist_setup()
     try:
         if args.impl == "reference":

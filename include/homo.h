@@ -79,6 +79,7 @@ typedef struct homo_opts {
   int post_sweeps;  /* smoothing sweeps after it (default 1; must equal pre_sweeps)      */
   int smoother;     /* HOMO_SMOOTH_GS8 (default) or HOMO_SMOOTH_CHEBYSHEV                */
   int cheb_degree;  /* Chebyshev polynomial degree per sweep, 2..4 (default 2)           */
+  int precision;    /* HOMO_PRECISION_FP32 (default) or HOMO_PRECISION_MIXED             */
 } homo_opts;
 
 /* Smoothers. GS8: 8-colour block Gauss-Seidel (Sec. 4.1-4.2, Eq. 15-16), colours 0..7
@@ -89,6 +90,19 @@ typedef struct homo_opts {
  * one data-parallel pass (not in the paper, which uses GS8). */
 #define HOMO_SMOOTH_GS8 0
 #define HOMO_SMOOTH_CHEBYSHEV 1
+
+/* Storage precision of the preconditioner's coarse-level stencils (the paper's mixed
+ * scheme keeps its numerical stencils in half precision and every vector in single
+ * precision, Sec. 4.1 "Mixed floating-point precision representations", Sec. 6.3).
+ * FP32: every stored stencil in FP32. MIXED: the stencils of the smoothed coarse levels
+ * are also kept as BF16 (FP32 exponent range: an FP16 copy would flush the void-region
+ * entries, ~E_min, to zero) and the coarse smoothers and residuals read that copy; each
+ * block is stored as the BF16 rounding of (A_d(v) + A_-d(v+d)^T) / 2, so the rounded
+ * coarse operators stay exactly symmetric. Arithmetic stays FP32, the Galerkin products
+ * are formed from the FP32 stencils, and the CG iteration (u, r, p, q, the true residual)
+ * is untouched: the solution meets the same tolerance; only the preconditioner changes. */
+#define HOMO_PRECISION_FP32 0
+#define HOMO_PRECISION_MIXED 1
 
 /* Library version as 10000*major + 100*minor + patch. */
 int homo_version(void);

@@ -55,7 +55,7 @@ void free_all(homo_ctx* c) {
   f(c->rho); f(c->E); f(c->u); f(c->ulo); f(c->f); f(c->r); f(c->z); f(c->pv); f(c->q);
   f(c->tmp); f(c->A); f(c->G); f(c->part); f(c->scal); f(c->ecyc); f(c->ecyclo);
   for (int l = 0; l < kMaxLevels; ++l) {
-    f(c->lev[l].st); f(c->lev[l].x); f(c->lev[l].b); f(c->lev[l].t);
+    f(c->lev[l].st); f(c->lev[l].x); f(c->lev[l].b); f(c->lev[l].t); f(c->lev[l].sth);
   }
   if (c->hscal) cudaFreeHost(c->hscal);
   for (auto& r : c->pending) {
@@ -173,6 +173,8 @@ int ensure_hierarchy(homo_ctx* c) {
     for (int l = 1; l + 1 < c->nlev; ++l) KL(c, HOMO_KC_SETUP, 1, launch_galerkin(c->lev[l], c->lev[l + 1], c->stream));
   }
   KL(c, HOMO_KC_SETUP, 3, launch_coarsest_setup(c));
+  for (int l = 1; l + 1 < c->nlev; ++l)
+    if (c->lev[l].sth) KL(c, HOMO_KC_SETUP, 1, launch_stencil_bf16(c->lev[l], c->stream));
   if (c->opts.smoother == HOMO_SMOOTH_CHEBYSHEV) RET(estimate_spectra(c));
   c->hier_valid = true;
   return HOMO_OK;
@@ -424,6 +426,7 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
   o.post_sweeps = 1;
   o.smoother = HOMO_SMOOTH_GS8;
   o.cheb_degree = 2;
+  o.precision = HOMO_PRECISION_FP32;
   if (opts) {
     if (opts->struct_size != static_cast<int>(sizeof(homo_opts)))
       return set_err(nullptr, HOMO_EINVAL, "homo_opts.struct_size mismatch");
@@ -433,13 +436,15 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
     if (opts->post_sweeps) o.post_sweeps = opts->post_sweeps;
     o.smoother = opts->smoother;
     if (opts->cheb_degree) o.cheb_degree = opts->cheb_degree;
+    o.precision = opts->precision;
   }
   if (o.min_coarse < 3 || o.max_levels < 0 || o.max_levels > kMaxLevels || o.pre_sweeps < 0 ||
       o.post_sweeps < 0 || o.pre_sweeps > 16 || o.post_sweeps > 16 || o.pre_sweeps != o.post_sweeps ||
       (o.smoother != HOMO_SMOOTH_GS8 && o.smoother != HOMO_SMOOTH_CHEBYSHEV) || o.cheb_degree < 2 ||
-      o.cheb_degree > 4)
+      o.cheb_degree > 4 || (o.precision != HOMO_PRECISION_FP32 && o.precision != HOMO_PRECISION_MIXED))
     return set_err(nullptr, HOMO_EINVAL,
-                   "bad homo_opts (min_coarse >= 3, pre == post sweeps <= 16, smoother 0/1, degree 2..4)");
+                   "bad homo_opts (min_coarse >= 3, pre == post sweeps <= 16, smoother 0/1, degree 2..4, "
+                   "precision 0/1)");
   int sizes[kMaxLevels];
   int nlev = 1;
   sizes[0] = n;
@@ -483,6 +488,8 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
     L.N = static_cast<size_t>(L.n) * L.n * L.n;
     L.colour_blocked = (L.n % 2 == 0);
     if (l >= 1 || nlev == 1) A(&L.st, kStencil * L.N, "stencil");
+    if (o.precision == HOMO_PRECISION_MIXED && l >= 1 && l + 1 < nlev && rc == HOMO_OK)
+      rc = dalloc(c, &L.sth, kStencil * L.N, "stencil (bf16)");
     if (l >= 1) {
       A(&L.x, kPlanes * L.N, "level x");
       A(&L.b, kPlanes * L.N, "level b");

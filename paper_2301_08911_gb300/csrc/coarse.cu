@@ -119,6 +119,39 @@ __global__ void __launch_bounds__(256) k_galerkin(const float* __restrict__ sf, 
   }
 }
 
+// Stencil entry as FP32 from FP32 or BF16 storage.
+__device__ __forceinline__ float ld_st(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ld_st(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+// Mixed precision: st16 = BF16 of (A_d(v) + A_-d(v+d)^T) / 2 for every vertex v and
+// neighbour d. Both partners of a pair are formed from the same two FP32 blocks (FP32
+// addition commutes and the halving is exact), so the rounded operator is exactly
+// symmetric. Thread per (d, position); writes the BF16 plane layout of st.
+__global__ void __launch_bounds__(256) k_stencil_bf16(const float* __restrict__ st, int n, bool cb,
+                                                      __nv_bfloat16* __restrict__ st16) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  const size_t total = 27 * N;
+  for (size_t it = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; it < total;
+       it += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const int d = static_cast<int>(it / N);
+    const size_t p = it - static_cast<size_t>(d) * N;
+    int X, Y, Z;
+    vertex_of_pos(p, n, cb, X, Y, Z);
+    const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+    const int Xn = (X + dx + n) % n, Yn = (Y + dy + n) % n, Zn = (Z + dz + n) % n;
+    const size_t pn = stencil_pos(Xn, Yn, Zn, n, cb);
+    const int dm = 26 - d;                      // offset -d seen from the neighbour
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float a = st[static_cast<size_t>(9 * d + 3 * r + c) * N + p];
+        const float b = st[static_cast<size_t>(9 * dm + 3 * c + r) * N + pn];
+        st16[static_cast<size_t>(9 * d + 3 * r + c) * N + p] = __float2bfloat16_rn(0.5f * (a + b));
+      }
+  }
+}
+
 __device__ __forceinline__ void solve3x6c(const float (&S)[9], float (&b)[18]) {
   const float d0 = S[0];
   const float l10 = S[3] / d0, l20 = S[6] / d0;
@@ -143,7 +176,8 @@ __device__ __forceinline__ void solve3x6c(const float (&S)[9], float (&b)[18]) {
 // One colour pass of block Gauss-Seidel (Eq. 15-16) with the stored stencil. Neighbours
 // have other colours and are not written during the pass. first != 0: first sweep from
 // x = 0 in colour order 0..7 (higher-colour neighbours are still zero and skipped).
-__global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_gs(const T* __restrict__ st,
                                                    const float* __restrict__ f,
                                                    float* __restrict__ x, int n, int colour,
                                                    int first) {
@@ -153,9 +187,9 @@ __global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
   const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
   for (size_t m = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < Nh;
        m += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int X = 2 * static_cast<int>(m % h) + cx;
-    const int Y = 2 * static_cast<int>((m / h) % h) + cy;
-    const int Z = 2 * static_cast<int>(m / (static_cast<size_t>(h) * h)) + cz;
+    int i, j, k;
+    decode3(static_cast<unsigned>(m), static_cast<unsigned>(h), i, j, k);
+    const int X = 2 * i + cx, Y = 2 * j + cy, Z = 2 * k + cz;
     const size_t p = static_cast<size_t>(colour) * Nh + m;
     const size_t v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
     const Nb nb = make_nb(X, Y, Z, n);
@@ -164,7 +198,7 @@ __global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
     for (int q = 0; q < kPlanes; ++q) rhs[q] = __ldg(f + q * N + v);
     float S[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) S[q] = __ldg(st + static_cast<size_t>(9 * 13 + q) * N + p);
+    for (int q = 0; q < 9; ++q) S[q] = ld_st(st + static_cast<size_t>(9 * 13 + q) * N + p);
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
       if (d == 13) continue;
@@ -173,7 +207,7 @@ __global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
       if (first && (colour ^ odd) > colour) continue;
       float A[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) A[q] = __ldg(st + static_cast<size_t>(9 * d + q) * N + p);
+      for (int q = 0; q < 9; ++q) A[q] = ld_st(st + static_cast<size_t>(9 * d + q) * N + p);
       const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
       const float* xr = x;
 #pragma unroll
@@ -182,7 +216,7 @@ __global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
                     u2 = __ldg(xr + (3 * c + 2) * N + w);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
-          rhs[3 * c + r] -= fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, A[3 * r + 2] * u2));
+          rhs[3 * c + r] = fmaf(-A[3 * r + 2], u2, fmaf(-A[3 * r + 1], u1, fmaf(-A[3 * r], u0, rhs[3 * c + r])));
       }
     }
     solve3x6c(S, rhs);
@@ -192,16 +226,19 @@ __global__ void __launch_bounds__(256) k_coarse_gs(const float* __restrict__ st,
 }
 
 // out = b - K x with the stored stencil; threads walk stencil positions (coalesced).
-__global__ void __launch_bounds__(256) k_coarse_residual(const float* __restrict__ st,
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_residual(const T* __restrict__ st,
                                                          const float* __restrict__ b,
                                                          const float* __restrict__ x,
                                                          float* __restrict__ out, int n, bool cb) {
   const size_t N = static_cast<size_t>(n) * n * n;
-  for (size_t p = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < N;
-       p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+  // vertices in lexicographic order: x, b and out are read and written in whole sectors;
+  // with colour-blocked stencils a warp's stencil reads are two contiguous runs
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
     int X, Y, Z;
-    vertex_of_pos(p, n, cb, X, Y, Z);
-    const size_t v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
+    decode3(static_cast<unsigned>(v), static_cast<unsigned>(n), X, Y, Z);
+    const size_t p = stencil_pos(X, Y, Z, n, cb);
     const Nb nb = make_nb(X, Y, Z, n);
     float acc[kPlanes];
 #pragma unroll
@@ -211,7 +248,7 @@ __global__ void __launch_bounds__(256) k_coarse_residual(const float* __restrict
       const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
       float A[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) A[q] = __ldg(st + static_cast<size_t>(9 * d + q) * N + p);
+      for (int q = 0; q < 9; ++q) A[q] = ld_st(st + static_cast<size_t>(9 * d + q) * N + p);
       const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
 #pragma unroll
       for (int c = 0; c < kCases; ++c) {
@@ -227,21 +264,22 @@ __global__ void __launch_bounds__(256) k_coarse_residual(const float* __restrict
   }
 }
 
-// Chebyshev step with the stored stencil (threads walk stencil positions):
+// Chebyshev step with the stored stencil (threads walk vertices in lexicographic order):
 // mode 0: out = x_in + c0 S^-1 (b - K x_in); mode 1: out = x_in + c0 (x_in - out) +
 // c1 S^-1 (b - K x_in), the previous iterate read from out and replaced in place.
 // x_in == null stands for x_in = 0 (first step from zero). mode 2: out = S^-1 K x_in
 // (power iteration for the largest eigenvalue of D^-1 K).
-__global__ void __launch_bounds__(256) k_coarse_cheb(const float* __restrict__ st,
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_cheb(const T* __restrict__ st,
                                                      const float* __restrict__ b,
                                                      const float* __restrict__ xin, float* out,
                                                      int n, bool cb, int mode, float c0, float c1) {
   const size_t N = static_cast<size_t>(n) * n * n;
-  for (size_t p = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; p < N;
-       p += static_cast<size_t>(gridDim.x) * blockDim.x) {
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
     int X, Y, Z;
-    vertex_of_pos(p, n, cb, X, Y, Z);
-    const size_t v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
+    decode3(static_cast<unsigned>(v), static_cast<unsigned>(n), X, Y, Z);
+    const size_t p = stencil_pos(X, Y, Z, n, cb);
     float acc[kPlanes];
 #pragma unroll
     for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
@@ -252,7 +290,7 @@ __global__ void __launch_bounds__(256) k_coarse_cheb(const float* __restrict__ s
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
         float A[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) A[q] = __ldg(st + static_cast<size_t>(9 * d + q) * N + p);
+        for (int q = 0; q < 9; ++q) A[q] = ld_st(st + static_cast<size_t>(9 * d + q) * N + p);
         const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
 #pragma unroll
         for (int c = 0; c < kCases; ++c) {
@@ -266,7 +304,7 @@ __global__ void __launch_bounds__(256) k_coarse_cheb(const float* __restrict__ s
     }
     float S[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) S[q] = __ldg(st + static_cast<size_t>(9 * 13 + q) * N + p);
+    for (int q = 0; q < 9; ++q) S[q] = ld_st(st + static_cast<size_t>(9 * 13 + q) * N + p);
     if (mode != 2) {
 #pragma unroll
       for (int q = 0; q < kPlanes; ++q) acc[q] = __ldg(b + q * N + v) - acc[q];
@@ -521,25 +559,29 @@ cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, cudaStream_t s) {
 
 cudaError_t launch_coarse_residual(const Level& L, const float* b, const float* x, float* out,
                                    cudaStream_t s) {
-  k_coarse_residual<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, b, x, out, L.n, L.colour_blocked);
+  if (L.sth) k_coarse_residual<<<grid_for(L.N, 256), 256, 0, s>>>(L.sth, b, x, out, L.n, L.colour_blocked);
+  else k_coarse_residual<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, b, x, out, L.n, L.colour_blocked);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x, int first,
                              cudaStream_t s) {
   const size_t h = static_cast<size_t>(L.n / 2);
-  k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.st, f, x, L.n, colour, first);
+  if (L.sth) k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.sth, f, x, L.n, colour, first);
+  else k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.st, f, x, L.n, colour, first);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_cheb(const Level& L, const float* b, const float* x_in, float* out, int mode,
                                float c0, float c1, cudaStream_t s) {
-  k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, b, x_in, out, L.n, L.colour_blocked, mode, c0, c1);
+  if (L.sth) k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.sth, b, x_in, out, L.n, L.colour_blocked, mode, c0, c1);
+  else k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, b, x_in, out, L.n, L.colour_blocked, mode, c0, c1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_coarse_dinvk(const Level& L, const float* x, float* y, cudaStream_t s) {
-  k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, nullptr, x, y, L.n, L.colour_blocked, 2, 0.f, 0.f);
+  if (L.sth) k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.sth, nullptr, x, y, L.n, L.colour_blocked, 2, 0.f, 0.f);
+  else k_coarse_cheb<<<grid_for(L.N, 256), 256, 0, s>>>(L.st, nullptr, x, y, L.n, L.colour_blocked, 2, 0.f, 0.f);
   return cudaGetLastError();
 }
 
@@ -583,6 +625,12 @@ cudaError_t launch_coarsest_apply(const homo_ctx* c, const float* b, float* x) {
   const int rows = kCases * c->mc;
   const int blocks = (rows * 32 + 255) / 256;
   k_coarsest_apply<<<blocks < 1216 ? blocks : 1216, 256, 0, c->stream>>>(c->G, c->mc, b, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stencil_bf16(const Level& L, cudaStream_t s) {
+  if (!L.sth || !L.st) return cudaErrorInvalidValue;
+  k_stencil_bf16<<<grid_for(27 * L.N, 256), 256, 0, s>>>(L.st, L.n, L.colour_blocked, L.sth);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,16 @@ namespace homo {
 
 constexpr int kGridCap = 152 * 16;   // 152 SMs on GB300, 16 resident 256-thread CTAs max
 
+// (i, j, k) of a linear index m = i + h (j + h k) in 32-bit arithmetic (m < 2^32: every
+// grid here has at most 1024^3 vertices): two divisions, remainders by products.
+__device__ __forceinline__ void decode3(unsigned m, unsigned h, int& i, int& j, int& k) {
+  const unsigned q = m / h;
+  const unsigned kk = q / h;
+  i = static_cast<int>(m - q * h);
+  j = static_cast<int>(q - kk * h);
+  k = static_cast<int>(kk);
+}
+
 // Wrapped coordinates x-1, x, x+1 premultiplied by the axis stride.
 struct Nb {
   int X[3];

@@ -87,9 +87,9 @@ __global__ void __launch_bounds__(256, 4) k_fine_gs(const __grid_constant__ KePa
   const int q0 = 3 * kGsCases * blockIdx.y;                // first plane of the case group
   for (size_t m = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < Nh;
        m += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = 2 * static_cast<int>(m % h) + cx;
-    const int y = 2 * static_cast<int>((m / h) % h) + cy;
-    const int z = 2 * static_cast<int>(m / (static_cast<size_t>(h) * h)) + cz;
+    int i, j, k;
+    decode3(static_cast<unsigned>(m), static_cast<unsigned>(h), i, j, k);
+    const int x = 2 * i + cx, y = 2 * j + cy, z = 2 * k + cz;
     const size_t v = static_cast<size_t>(x) + static_cast<size_t>(n) * (y + static_cast<size_t>(n) * z);
     const Nb nb = make_nb(x, y, z, n);
     float Et[8];
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256, 4) k_fine_gs(const __grid_constant__ KePa
                     u2 = __ldg(ur + (3 * c + 2) * N);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
-          rhs[3 * c + r] -= fmaf(A[3 * r], u0, fmaf(A[3 * r + 1], u1, A[3 * r + 2] * u2));
+          rhs[3 * c + r] = fmaf(-A[3 * r + 2], u2, fmaf(-A[3 * r + 1], u1, fmaf(-A[3 * r], u0, rhs[3 * c + r])));
       }
     }
     float S[9];

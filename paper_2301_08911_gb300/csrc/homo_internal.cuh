@@ -10,6 +10,7 @@
 //     plane; x-fastest order when n_l is odd (only possible on the coarsest level).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -58,6 +59,8 @@ struct Level {
   size_t N = 0;
   bool colour_blocked = false;
   float* st = nullptr;   // 243 * N (levels >= 1)
+  __nv_bfloat16* sth = nullptr;   // symmetrised BF16 copy of st (mixed precision, smoothed
+                                  // coarse levels), read by the coarse smoothers/residual
   float* x = nullptr;    // 18 * N (levels >= 1)
   float* b = nullptr;    // 18 * N (levels >= 1)
   float* t = nullptr;    // 18 * N residual scratch (levels >= 1)
@@ -176,6 +179,8 @@ cudaError_t launch_coarse_cheb(const Level& L, const float* b, const float* x_in
                                float c0, float c1, cudaStream_t s);
 // y = S^-1 K x on a stored-stencil level (power iteration for the Chebyshev interval)
 cudaError_t launch_coarse_dinvk(const Level& L, const float* x, float* y, cudaStream_t s);
+// mixed precision: L.sth = symmetrised BF16 copy of L.st
+cudaError_t launch_stencil_bf16(const Level& L, cudaStream_t s);
 cudaError_t launch_fill_hash(float* x, size_t count, unsigned seed, cudaStream_t s);
 // largest eigenvalue of blockdiag(K0)^-1 K0 (host arithmetic)
 double element_jacobi_bound(const KeParam& ke);

@@ -9,40 +9,110 @@ namespace homo {
 
 namespace {
 
+// W consecutive floats (W = 4: one 16-byte access; the caller guarantees alignment, i.e.
+// N % 4 == 0 so that every plane starts on a 16-byte boundary).
+template <int W>
+struct Pk {
+  float v[W];
+};
+
+template <int W>
+__device__ __forceinline__ Pk<W> ldg_pk(const float* __restrict__ p) {
+  Pk<W> r;
+  if constexpr (W == 4) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else {
+    r.v[0] = __ldg(p);
+  }
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ Pk<W> ld_pk(const float* p) {
+  Pk<W> r;
+  if constexpr (W == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+  } else {
+    r.v[0] = *p;
+  }
+  return r;
+}
+
+template <int W>
+__device__ __forceinline__ void st_pk(float* p, const Pk<W>& x) {
+  if constexpr (W == 4) *reinterpret_cast<float4*>(p) = make_float4(x.v[0], x.v[1], x.v[2], x.v[3]);
+  else *p = x.v[0];
+}
+
+// hi + lo += d + dlo in double-float (TwoSum, then FastTwoSum renormalisation), with
+// operations the compiler may not contract or reorder.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float d, float dlo) {
+  const float sm = __fadd_rn(hi, d);
+  const float bb = __fadd_rn(sm, -hi);
+  const float er = __fadd_rn(__fadd_rn(hi, -__fadd_rn(sm, -bb)), __fadd_rn(d, -bb));
+  const float l = __fadd_rn(__fadd_rn(lo, dlo), er);
+  const float s2 = __fadd_rn(sm, l);
+  lo = __fadd_rn(l, -__fadd_rn(s2, -sm));
+  hi = s2;
+}
+
 __global__ void __launch_bounds__(256) k_sum_partials(const double* __restrict__ part, int nblk,
                                                       int nv, double* __restrict__ out) {
+  // thread t owns value k = t % nv of rows r0, r0 + per, r0 + 2 per, ... (r0 = t / nv):
+  // the block reads the row-major partials contiguously, with four independent sums
   __shared__ double sh[256];
-  for (int k = 0; k < nv; ++k) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += part[static_cast<size_t>(b) * nv + k];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-      __syncthreads();
+  const int t = threadIdx.x;
+  const int per = blockDim.x / nv;
+  const int k = t % nv, r0 = t / nv;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  if (r0 < per) {
+    const size_t stride = static_cast<size_t>(per) * nv;
+    const size_t total = static_cast<size_t>(nblk) * nv;
+    size_t i = static_cast<size_t>(r0) * nv + k;
+    for (; i + 3 * stride < total; i += 4 * stride) {
+      s0 += part[i];
+      s1 += part[i + stride];
+      s2 += part[i + 2 * stride];
+      s3 += part[i + 3 * stride];
     }
-    if (threadIdx.x == 0) out[k] = sh[0];
-    __syncthreads();
+    for (; i < total; i += stride) s0 += part[i];
+  }
+  sh[t] = (s0 + s1) + (s2 + s3);
+  __syncthreads();
+  if (t < nv) {
+    double acc = 0.0;
+    for (int r = 0; r < per; ++r) acc += sh[r * nv + t];
+    out[t] = acc;
   }
 }
 
-// Per case c: sum over the 3 planes of case c of a*b.
+// Per case c: sum over the 3 planes of case c of a*b. Each thread takes W consecutive
+// vertices per step (W = 4: 16-byte accesses, four times the bytes in flight).
+template <int W>
 __global__ void __launch_bounds__(256) k_dot6(const float* __restrict__ a,
                                               const float* __restrict__ b, size_t N,
                                               double* __restrict__ part) {
   float red[kCases];
 #pragma unroll
   for (int c = 0; c < kCases; ++c) red[c] = 0.f;
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N / W;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = i * W;
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) red[q / 3] = fmaf(__ldg(a + q * N + v), __ldg(b + q * N + v), red[q / 3]);
+    for (int q = 0; q < kPlanes; ++q) {
+      const Pk<W> x = ldg_pk<W>(a + q * N + v), y = ldg_pk<W>(b + q * N + v);
+#pragma unroll
+      for (int w = 0; w < W; ++w) red[q / 3] = fmaf(x.v[w], y.v[w], red[q / 3]);
+    }
   }
   block_sum_store<kCases>(red, part);
 }
 
 // (r_c - mean r, z_c) for the 6 cases and the 18 plane sums of z (for removing its mean).
 // rmean: 18 plane means of r (doubles), or null.
+template <int W>
 __global__ void __launch_bounds__(256) k_dot6_zsum(const float* __restrict__ r,
                                                    const float* __restrict__ z, size_t N,
                                                    const double* __restrict__ rmean,
@@ -52,13 +122,17 @@ __global__ void __launch_bounds__(256) k_dot6_zsum(const float* __restrict__ r,
   for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
 #pragma unroll
   for (int q = 0; q < kPlanes; ++q) rm[q] = rmean ? static_cast<float>(rmean[q]) : 0.f;
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N / W;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = i * W;
 #pragma unroll
     for (int q = 0; q < kPlanes; ++q) {
-      const float zz = __ldg(z + q * N + v);
-      red[q / 3] = fmaf(__ldg(r + q * N + v) - rm[q], zz, red[q / 3]);
-      red[kCases + q] += zz;
+      const Pk<W> zz = ldg_pk<W>(z + q * N + v), rr = ldg_pk<W>(r + q * N + v);
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        red[q / 3] = fmaf(rr.v[w] - rm[q], zz.v[w], red[q / 3]);
+        red[kCases + q] += zz.v[w];
+      }
     }
   }
   block_sum_store<kCases + kPlanes>(red, part);
@@ -109,6 +183,7 @@ __global__ void k_cg_active(double* __restrict__ s, double tol2, double N) {
 // noise would be amplified by the operator's spread of eigenvalues and leave the true
 // residual far above the recursive one. r -= alpha (q - mean q) in FP32. Partial sums of
 // ||r_c||^2 and of the 18 plane sums of r.
+template <int W>
 __global__ void __launch_bounds__(256) k_cg_update_er(float* __restrict__ e, float* __restrict__ elo,
                                                       float* __restrict__ r,
                                                       const float* __restrict__ p,
@@ -123,58 +198,63 @@ __global__ void __launch_bounds__(256) k_cg_update_er(float* __restrict__ e, flo
   for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
 #pragma unroll
   for (int k = 0; k < kPlanes; ++k) qm[k] = static_cast<float>(s[S_QSUM + k] / static_cast<double>(N));
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N / W;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = i * W;
 #pragma unroll
     for (int k = 0; k < kPlanes; ++k) {
       const int c = k / 3;
       const size_t o = static_cast<size_t>(k) * N + v;
-      float rv = r[o];
+      Pk<W> rv = ld_pk<W>(r + o);
       if (a[c] != 0.f) {
-        const float pv = __ldg(p + o);
-        const float pr = __fmul_rn(a[c], pv);              // TwoProd: pr + pe = a p exactly
-        const float pe = fmaf(a[c], pv, -pr);
-        const float hi = e[o];
-        const float sm = __fadd_rn(hi, pr);                // TwoSum(hi, pr)
-        const float bb = __fadd_rn(sm, -hi);
-        const float er = __fadd_rn(__fadd_rn(hi, -__fadd_rn(sm, -bb)), __fadd_rn(pr, -bb));
-        const float lo = __fadd_rn(__fadd_rn(elo[o], pe), er);
-        const float s2 = __fadd_rn(sm, lo);                // FastTwoSum renormalisation
-        e[o] = s2;
-        elo[o] = __fadd_rn(lo, -__fadd_rn(s2, -sm));
-        rv = fmaf(-a[c], __ldg(q + o) - qm[k], rv);
-        r[o] = rv;
+        const Pk<W> pv = ldg_pk<W>(p + o), qv = ldg_pk<W>(q + o);
+        Pk<W> hi = ld_pk<W>(e + o), lo = ld_pk<W>(elo + o);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+          const float pr = __fmul_rn(a[c], pv.v[w]);        // TwoProd: pr + pe = a p exactly
+          const float pe = fmaf(a[c], pv.v[w], -pr);
+          df_add(hi.v[w], lo.v[w], pr, pe);
+          rv.v[w] = fmaf(-a[c], qv.v[w] - qm[k], rv.v[w]);
+        }
+        st_pk<W>(e + o, hi);
+        st_pk<W>(elo + o, lo);
+        st_pk<W>(r + o, rv);
       }
-      red[c] = fmaf(rv, rv, red[c]);
-      red[kCases + k] += rv;
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        red[c] = fmaf(rv.v[w], rv.v[w], red[c]);
+        red[kCases + k] += rv.v[w];
+      }
     }
   }
   block_sum_store<kCases + kPlanes>(red, part);
 }
 
 // (u + ulo) += (e + elo) in double-float arithmetic (error-free transformations with
-// non-contracted operations), then e = elo = 0. Closes a CG cycle.
+// non-contracted operations), then e = elo = 0. Closes a CG cycle. n % W == 0.
+template <int W>
 __global__ void __launch_bounds__(256) k_fold(float* __restrict__ u, float* __restrict__ ulo,
                                               float* __restrict__ e, float* __restrict__ elo,
                                               size_t n) {
-  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+  Pk<W> zero;
+#pragma unroll
+  for (int w = 0; w < W; ++w) zero.v[w] = 0.f;
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n / W;
        i += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const float d = e[i], dlo = elo[i];
-    if (d == 0.f && dlo == 0.f) continue;
-    const float hi = u[i];
-    const float sm = __fadd_rn(hi, d);                   // TwoSum(hi, d)
-    const float bb = __fadd_rn(sm, -hi);
-    const float er = __fadd_rn(__fadd_rn(hi, -__fadd_rn(sm, -bb)), __fadd_rn(d, -bb));
-    const float lo = __fadd_rn(__fadd_rn(ulo[i], dlo), er);
-    const float s2 = __fadd_rn(sm, lo);                  // FastTwoSum renormalisation
-    u[i] = s2;
-    ulo[i] = __fadd_rn(lo, -__fadd_rn(s2, -sm));
-    e[i] = 0.f;
-    elo[i] = 0.f;
+    const size_t o = i * W;
+    const Pk<W> d = ld_pk<W>(e + o), dlo = ld_pk<W>(elo + o);
+    Pk<W> hi = ld_pk<W>(u + o), lo = ld_pk<W>(ulo + o);
+#pragma unroll
+    for (int w = 0; w < W; ++w) df_add(hi.v[w], lo.v[w], d.v[w], dlo.v[w]);
+    st_pk<W>(u + o, hi);
+    st_pk<W>(ulo + o, lo);
+    st_pk<W>(e + o, zero);
+    st_pk<W>(elo + o, zero);
   }
 }
 
 // p = (z - mean(z)) + beta p per plane.
+template <int W>
 __global__ void __launch_bounds__(256) k_cg_update_p(float* __restrict__ p,
                                                      const float* __restrict__ z,
                                                      const double* __restrict__ s, size_t N) {
@@ -183,13 +263,23 @@ __global__ void __launch_bounds__(256) k_cg_update_p(float* __restrict__ p,
   for (int c = 0; c < kCases; ++c) b[c] = static_cast<float>(s[S_BETA + c]);
 #pragma unroll
   for (int k = 0; k < kPlanes; ++k) mz[k] = static_cast<float>(s[S_ZSUM + k] / static_cast<double>(N));
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+  for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < N / W;
+       i += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const size_t v = i * W;
 #pragma unroll
     for (int k = 0; k < kPlanes; ++k) {
       const size_t o = static_cast<size_t>(k) * N + v;
-      const float zz = __ldg(z + o) - mz[k];
-      p[o] = b[k / 3] != 0.f ? fmaf(b[k / 3], p[o], zz) : zz;
+      const Pk<W> zz = ldg_pk<W>(z + o);
+      Pk<W> pp;
+      if (b[k / 3] != 0.f) {
+        pp = ld_pk<W>(p + o);
+#pragma unroll
+        for (int w = 0; w < W; ++w) pp.v[w] = fmaf(b[k / 3], pp.v[w], zz.v[w] - mz[k]);
+      } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w) pp.v[w] = zz.v[w] - mz[k];
+      }
+      st_pk<W>(p + o, pp);
     }
   }
 }
@@ -406,23 +496,26 @@ int reduce_grid(size_t n_items) { return grid_for(n_items, 256); }
 
 cudaError_t launch_sum_partials(const double* part, int nblk, int nv, double* out,
                                 cudaStream_t s) {
+  if (nv < 1 || nv > 256) return cudaErrorInvalidValue;
   k_sum_partials<<<1, 256, 0, s>>>(part, nblk, nv, out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot6(const float* a, const float* b, size_t N, double* part, int* grid_out,
                         cudaStream_t s) {
-  const int g = grid_for(N, 256);
+  const int g = grid_for(N % 4 == 0 ? N / 4 : N, 256);
   *grid_out = g;
-  k_dot6<<<g, 256, 0, s>>>(a, b, N, part);
+  if (N % 4 == 0) k_dot6<4><<<g, 256, 0, s>>>(a, b, N, part);
+  else k_dot6<1><<<g, 256, 0, s>>>(a, b, N, part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_dot6_zsum(const float* r, const float* z, size_t N, const double* rmean,
                              double* part, int* grid_out, cudaStream_t s) {
-  const int g = grid_for(N, 256);
+  const int g = grid_for(N % 4 == 0 ? N / 4 : N, 256);
   *grid_out = g;
-  k_dot6_zsum<<<g, 256, 0, s>>>(r, z, N, rmean, part);
+  if (N % 4 == 0) k_dot6_zsum<4><<<g, 256, 0, s>>>(r, z, N, rmean, part);
+  else k_dot6_zsum<1><<<g, 256, 0, s>>>(r, z, N, rmean, part);
   return cudaGetLastError();
 }
 
@@ -444,20 +537,23 @@ cudaError_t launch_cg_active(double* scal, double tol, size_t N, cudaStream_t s)
 cudaError_t launch_cg_update_er(float* e, float* elo, float* r, const float* p, const float* q,
                                 const double* scal, size_t N, double* part, int* grid_out,
                                 cudaStream_t s) {
-  const int g = grid_for(N, 256);
+  const int g = grid_for(N % 4 == 0 ? N / 4 : N, 256);
   *grid_out = g;
-  k_cg_update_er<<<g, 256, 0, s>>>(e, elo, r, p, q, scal, N, part);
+  if (N % 4 == 0) k_cg_update_er<4><<<g, 256, 0, s>>>(e, elo, r, p, q, scal, N, part);
+  else k_cg_update_er<1><<<g, 256, 0, s>>>(e, elo, r, p, q, scal, N, part);
   return cudaGetLastError();
 }
 
 cudaError_t launch_fold(float* u, float* ulo, float* e, float* elo, size_t n, cudaStream_t s) {
-  k_fold<<<grid_for(n, 256), 256, 0, s>>>(u, ulo, e, elo, n);
+  if (n % 4 == 0) k_fold<4><<<grid_for(n / 4, 256), 256, 0, s>>>(u, ulo, e, elo, n);
+  else k_fold<1><<<grid_for(n, 256), 256, 0, s>>>(u, ulo, e, elo, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_update_p(float* p, const float* z, const double* scal, size_t N,
                                cudaStream_t s) {
-  k_cg_update_p<<<grid_for(N, 256), 256, 0, s>>>(p, z, scal, N);
+  if (N % 4 == 0) k_cg_update_p<4><<<grid_for(N / 4, 256), 256, 0, s>>>(p, z, scal, N);
+  else k_cg_update_p<1><<<grid_for(N, 256), 256, 0, s>>>(p, z, scal, N);
   return cudaGetLastError();
 }
 

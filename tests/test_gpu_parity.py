@@ -141,9 +141,14 @@ def test_gauss_seidel_sweep_matches_oracle(B, level, reverse):
     assert rel(dofs(host(ut).reshape(18, -1), nl), ref) < 2e-6
 
 
-@pytest.mark.parametrize("smoother,n", [("gs8", 16), ("chebyshev", 16), ("chebyshev", 24)])
-def test_vcycle_is_symmetric_positive(B, smoother, n):
-    hom = make(B, n, smoother=smoother)
+@pytest.mark.parametrize("smoother,n,precision", [("gs8", 16, "fp32"), ("chebyshev", 16, "fp32"),
+                                                 ("chebyshev", 24, "fp32"), ("gs8", 24, "mixed"),
+                                                 ("chebyshev", 16, "mixed")])
+def test_vcycle_is_symmetric_positive(B, smoother, n, precision):
+    """The preconditioner CG needs: (y, M x) = (x, M y) and (x, M x) > 0. With mixed
+    precision the BF16 coarse stencils are symmetrised before rounding, so the bound is
+    the same."""
+    hom = make(B, n, smoother=smoother, precision=precision)
     hom.set_density(cuda(smoothed_threshold_density(n, 0.3, 1)))
     x = mean_free(uniform_field(18 * n ** 3, 600, -1, 1).reshape(18, -1).astype(np.float64))
     y = mean_free(uniform_field(18 * n ** 3, 601, -1, 1).reshape(18, -1).astype(np.float64))
@@ -162,8 +167,8 @@ def test_vcycle_is_symmetric_positive(B, smoother, n):
 _CASES = {}
 
 
-def _solved(B, n, kind, smoother="gs8"):
-    key = (n, kind, smoother)
+def _solved(B, n, kind, smoother="gs8", precision="fp32"):
+    key = (n, kind, smoother, precision)
     if key in _CASES:
         return _CASES[key]
     if kind == "c1":
@@ -172,7 +177,7 @@ def _solved(B, n, kind, smoother="gs8"):
         rho = uniform_density(n, 700 + n, 0.05, 1.0)
     rho_t = oracle.cone_filter(rho, n, 2.0).astype(np.float32)
     ref = oracle.homogenize(rho_t.astype(np.float64), n)
-    hom = make(B, n, smoother=smoother)
+    hom = make(B, n, smoother=smoother, precision=precision)
     hom.set_density(cuda(rho_t))
     # well below the configs' 1e-6 so that the comparison measures the kernels' FP32
     # arithmetic, not the stopping tolerance (the sensitivity error is first order in it)
@@ -181,11 +186,15 @@ def _solved(B, n, kind, smoother="gs8"):
     return _CASES[key]
 
 
-@pytest.mark.parametrize("n,kind,smoother", [(16, "c1", "gs8"), (20, "uniform", "gs8"), (24, "uniform", "gs8"),
-                                             (12, "uniform", "gs8"), (16, "c1", "chebyshev"),
-                                             (24, "uniform", "chebyshev")])
-def test_CH_matches_oracle(B, n, kind, smoother):
-    hom, rho_t, ref, its, relres = _solved(B, n, kind, smoother)
+@pytest.mark.parametrize("n,kind,smoother,precision",
+                         [(16, "c1", "gs8", "fp32"), (20, "uniform", "gs8", "fp32"), (24, "uniform", "gs8", "fp32"),
+                          (12, "uniform", "gs8", "fp32"), (16, "c1", "chebyshev", "fp32"),
+                          (24, "uniform", "chebyshev", "fp32"), (16, "c1", "gs8", "mixed"),
+                          (24, "uniform", "gs8", "mixed"), (32, "c1", "chebyshev", "mixed")])
+def test_CH_matches_oracle(B, n, kind, smoother, precision):
+    """C^H against the FP64 oracle at 1e-6; with mixed precision only the preconditioner
+    changes, so the bar is the same."""
+    hom, rho_t, ref, its, relres = _solved(B, n, kind, smoother, precision)
     assert max(relres) <= 1e-9
     assert hom.residual_history().shape[1] == 6
     C = hom.CH()
@@ -351,13 +360,13 @@ def test_oc_unattainable_volume_goes_to_bounds(B):
 
 
 # ---------------------------------------------------------------- whole iteration
-@pytest.mark.parametrize("smoother", ["gs8", "chebyshev"])
-def test_full_iteration_matches_oracle_16(B, smoother):
+@pytest.mark.parametrize("smoother,precision", [("gs8", "fp32"), ("chebyshev", "fp32"), ("gs8", "mixed")])
+def test_full_iteration_matches_oracle_16(B, smoother, precision):
     """One bulk-modulus iteration at 16^3 on the blurred-noise cell at volume fraction 0.3."""
     n, V = 16, 0.3
     rho = smoothed_threshold_density(n, V, 1)
     ref = oracle.optimization_iteration(rho.astype(np.float64), n, V, "bulk")
-    hom = make(B, n, smoother=smoother)
+    hom = make(B, n, smoother=smoother, precision=precision)
     r = cuda(rho)
     rt = torch.empty_like(r)
     hom.filter(2.0, r, rt)
