@@ -16,6 +16,8 @@ The oracle is the plain definition of what the method computes, written from the
                Sec. 6.4 periodic kernel).
 * optim.py   - OC volume-constrained update (Sec. 3.3), objectives (Eq. 19-22), one
                whole optimisation iteration.
+* symmetry.py - orbit averaging under the reflect3 / rotate3 / reflect6 symmetry
+               groups (Sec. 6.1).
 * mg.py      - explicit trilinear prolongation, Galerkin coarse operators R K I and their
                27-block vertex stencils (Sec. 3.3, Eq. 17-18), 8-colour block Gauss-Seidel
                (Eq. 15-16).
@@ -42,6 +44,7 @@ from .fem import (  # noqa: F401
     homogenize,
 )
 from .filters import cone_filter, cone_weights  # noqa: F401
+from .symmetry import symmetrize  # noqa: F401
 from .optim import oc_update, objective, optimization_iteration  # noqa: F401
 from .mg import (  # noqa: F401
     prolongation,

@@ -479,3 +479,74 @@ def test_gs_colour_pass_zeroes_its_rows_and_descends():
         assert np.abs((f - K @ u1)[rows]).max() < 1e-12
         assert energy(u1) <= energy(u) + 1e-15
         u = u1
+
+
+# ---------------------------------------------------------------- symmetry (Sec. 6.1)
+def _generators(kind, n):
+    """Element maps named by the paper: mid-plane reflections; quarter turns about the
+    three axes through the centre; reflections in the diagonal planes x = y, y = z, z = x."""
+    refl = [lambda e, k=k: tuple(n - 1 - e[i] if i == k else e[i] for i in range(3)) for k in range(3)]
+    # quarter turn about axis k: (a, b) -> (n-1-b, a) in the plane of the other two axes
+    def quarter(k):
+        a, b = [i for i in range(3) if i != k]
+
+        def f(e):
+            out = list(e)
+            out[a], out[b] = n - 1 - e[b], e[a]
+            return tuple(out)
+        return f
+    diag = [lambda e, a=a, b=b: tuple(e[b] if i == a else e[a] if i == b else e[i] for i in range(3))
+            for a, b in ((0, 1), (1, 2), (0, 2))]
+    return {"reflect3": refl, "rotate3": [quarter(k) for k in range(3)], "reflect6": refl + diag}[kind]
+
+
+def _orbit(e, gens):
+    seen, todo = {e}, [e]
+    while todo:
+        x = todo.pop()
+        for g in gens:
+            y = g(x)
+            if y not in seen:
+                seen.add(y)
+                todo.append(y)
+    return seen
+
+
+@pytest.mark.parametrize("kind", ["reflect3", "rotate3", "reflect6"])
+@pytest.mark.parametrize("n", [4, 5])
+def test_symmetrize_is_the_orbit_average_of_the_named_generators(kind, n):
+    rng = np.random.default_rng(7 + n)
+    x = rng.random(n ** 3)
+    gens = _generators(kind, n)
+    want = np.empty_like(x)
+    for z in range(n):
+        for y in range(n):
+            for xx in range(n):
+                orb = _orbit((xx, y, z), gens)
+                want[xx + n * (y + n * z)] = np.mean([x[a + n * (b + n * c)] for a, b, c in orb])
+    assert np.abs(oracle.symmetrize(x, n, kind) - want).max() < 1e-14
+
+
+def test_symmetry_groups_have_the_cube_orders():
+    from oracle import symmetry
+    assert [len(symmetry.group(k)) for k in ("reflect3", "rotate3", "reflect6")] == [8, 24, 48]
+    # the orbit of a generic element under each generator set has the group's order
+    n = 9
+    for kind, order in (("reflect3", 8), ("rotate3", 24), ("reflect6", 48)):
+        assert len(_orbit((1, 2, 3), _generators(kind, n))) == order
+
+
+@pytest.mark.parametrize("kind", ["reflect3", "rotate3", "reflect6"])
+def test_symmetrize_is_an_invariant_projection_preserving_volume(kind):
+    n = 6
+    x = np.random.default_rng(3).random(n ** 3)
+    y = oracle.symmetrize(x, n, kind)
+    assert abs(y.mean() - x.mean()) < 1e-15
+    assert np.abs(oracle.symmetrize(y, n, kind) - y).max() < 1e-15
+    Y = y.reshape(n, n, n)
+    for g in _generators(kind, n):
+        for z in range(n):
+            for yy in range(n):
+                for xx in range(n):
+                    a, b, c = g((xx, yy, z))
+                    assert Y[z, yy, xx] == pytest.approx(Y[c, b, a], abs=1e-15)
