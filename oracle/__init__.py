@@ -13,7 +13,8 @@ The oracle is the plain definition of what the method computes, written from the
                (Eq. 4, Eq. 12), direct solve (Eq. 5), C^H (Eq. 7), sensitivities
                (Eq. 8, Eq. 9), the vertex form of K u (Eq. 13) for sampled vertices.
 * filters.py - periodic linear-cone density filter (Sec. 5 material interpolation,
-               Sec. 6.4 periodic kernel).
+               Sec. 6.4 periodic kernel) and the density-weighted sensitivity filter of
+               the unfiltered variant (Sec. 5.3).
 * optim.py   - OC volume-constrained update (Sec. 3.3), objectives (Eq. 19-22), one
                whole optimisation iteration.
 * symmetry.py - orbit averaging under the reflect3 / rotate3 / reflect6 symmetry
@@ -43,7 +44,7 @@ from .fem import (  # noqa: F401
     macro_strain_loads_at_vertices,
     homogenize,
 )
-from .filters import cone_filter, cone_weights  # noqa: F401
+from .filters import cone_filter, cone_weights, sensitivity_filter  # noqa: F401
 from .symmetry import symmetrize  # noqa: F401
 from .optim import oc_update, objective, optimization_iteration  # noqa: F401
 from .mg import (  # noqa: F401

@@ -34,3 +34,14 @@ def cone_filter(x: np.ndarray, n: int, radius: float = 2.0) -> np.ndarray:
         acc += w * np.roll(g, shift=(-dz, -dy, -dx), axis=(0, 1, 2))
         wsum += w
     return (acc / wsum).reshape(-1)
+
+
+def sensitivity_filter(rho: np.ndarray, dc: np.ndarray, n: int, radius: float = 2.0,
+                       gamma: float = 1e-3) -> np.ndarray:
+    """Density-weighted sensitivity filter of the unfiltered variant (Sec. 5.3: densities
+    penalised directly, sensitivities filtered before the OC update). The paper names the
+    step only; it is read as the classic mesh-independence filter
+        out_e = sum_f w(e - f) rho_f dc_f / (max(gamma, rho_e) sum_f w(e - f)),
+    with the same periodic linear cone as the density filter."""
+    r = np.asarray(rho, dtype=np.float64)
+    return cone_filter(r * np.asarray(dc, dtype=np.float64), n, radius) / np.maximum(gamma, r)

@@ -550,3 +550,37 @@ def test_symmetrize_is_an_invariant_projection_preserving_volume(kind):
                 for xx in range(n):
                     a, b, c = g((xx, yy, z))
                     assert Y[z, yy, xx] == pytest.approx(Y[c, b, a], abs=1e-15)
+
+
+# ---------------------------------------------------------------- sensitivity filter (Sec. 5.3)
+def test_sensitivity_filter_brute_force():
+    n, R = 4, 1.5
+    rng = np.random.default_rng(11)
+    rho, dc = rng.uniform(1e-4, 1, n ** 3), -rng.random(n ** 3)
+    want = np.empty(n ** 3)
+    for z in range(n):
+        for y in range(n):
+            for x in range(n):
+                num = den = 0.0
+                for dz in range(-2, 3):
+                    for dy in range(-2, 3):
+                        for dx in range(-2, 3):
+                            w = max(0.0, R - np.sqrt(dx * dx + dy * dy + dz * dz))
+                            f = (x + dx) % n + n * ((y + dy) % n + n * ((z + dz) % n))
+                            num += w * rho[f] * dc[f]
+                            den += w
+                e = x + n * (y + n * z)
+                want[e] = num / (max(1e-3, rho[e]) * den)
+    assert np.abs(oracle.sensitivity_filter(rho, dc, n, R) - want).max() < 1e-14
+
+
+def test_sensitivity_filter_special_cases():
+    n = 6
+    rng = np.random.default_rng(12)
+    dc = -rng.random(n ** 3)
+    # uniform density: the density filter of dc
+    assert np.abs(oracle.sensitivity_filter(np.full(n ** 3, 0.4), dc, n) - oracle.cone_filter(dc, n)).max() < 1e-15
+    # constant sensitivity: dc times the filtered density over the clamped density
+    rho = rng.uniform(1e-5, 1, n ** 3)
+    got = oracle.sensitivity_filter(rho, np.full(n ** 3, -2.0), n)
+    assert np.abs(got - (-2.0) * oracle.cone_filter(rho, n) / np.maximum(1e-3, rho)).max() < 1e-13
