@@ -17,6 +17,7 @@ The oracle is the plain definition of what the method computes, written from the
                the unfiltered variant (Sec. 5.3).
 * optim.py   - OC volume-constrained update (Sec. 3.3), objectives (Eq. 19-22), one
                whole optimisation iteration.
+* init.py    - trigonometric density initialisation with sigmoid projection (Sec. 6.2).
 * symmetry.py - orbit averaging under the reflect3 / rotate3 / reflect6 symmetry
                groups (Sec. 6.1).
 * mg.py      - explicit trilinear prolongation, Galerkin coarse operators R K I and their
@@ -46,6 +47,7 @@ from .fem import (  # noqa: F401
 )
 from .filters import cone_filter, cone_weights, sensitivity_filter  # noqa: F401
 from .symmetry import symmetrize  # noqa: F401
+from .init import trig_initialization  # noqa: F401
 from .optim import oc_update, objective, optimization_iteration  # noqa: F401
 from .mg import (  # noqa: F401
     prolongation,

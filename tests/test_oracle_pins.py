@@ -584,3 +584,43 @@ def test_sensitivity_filter_special_cases():
     rho = rng.uniform(1e-5, 1, n ** 3)
     got = oracle.sensitivity_filter(rho, np.full(n ** 3, -2.0), n)
     assert np.abs(got - (-2.0) * oracle.cone_filter(rho, n) / np.maximum(1e-3, rho)).max() < 1e-13
+
+
+# ---------------------------------------------------------------- trigonometric initialisation (Sec. 6.2)
+def test_quaternion_rotation_is_a_rotation_and_matches_axis_angle():
+    from oracle import init
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        R = init.quaternion_rotation(rng.uniform(-1, 1, 4))
+        assert np.abs(R @ R.T - np.eye(3)).max() < 1e-14 and abs(np.linalg.det(R) - 1) < 1e-14
+    t = 0.7
+    R = init.quaternion_rotation([np.cos(t / 2), 0, 0, np.sin(t / 2)])
+    want = np.array([[np.cos(t), -np.sin(t), 0], [np.sin(t), np.cos(t), 0], [0, 0, 1]])
+    assert np.abs(R - want).max() < 1e-15
+
+
+def test_trig_basis_at_identity_rotation():
+    from oracle import init
+    n, nb = 5, 2
+    B = init.trig_basis(n, nb, [1, 0, 0, 0])
+    assert B.shape == (n ** 3, init.basis_count(nb)) and init.basis_count(1) == 27 and init.basis_count(2) == 90
+    e = np.arange(n ** 3)
+    xc = (e % n + 0.5) / n - 0.5
+    zc = (e // (n * n) + 0.5) / n - 0.5
+    assert np.abs(B[:, 0] - np.cos(2 * np.pi * xc)).max() < 1e-14            # k=1, axis 0, cos
+    assert np.abs(B[:, 11] - np.sin(4 * np.pi * zc)).max() < 1e-14           # k=2, axis 2, sin
+    assert np.abs(B[:, 12] - np.cos(2 * np.pi * xc) ** 2).max() < 1e-14      # first product: T0 T0
+    assert np.abs(B[:, 13] - np.cos(2 * np.pi * xc) * np.sin(2 * np.pi * xc)).max() < 1e-14
+
+
+def test_trig_initialization_volume_bounds_and_zero_weights():
+    from oracle import init
+    n, nb, V = 6, 2, 0.3
+    rng = np.random.default_rng(22)
+    rho = init.trig_initialization(n, nb, rng.uniform(-1, 1, 4), rng.uniform(-1, 1, init.basis_count(nb)), V)
+    assert abs(rho.mean() - V) < 1e-12 and rho.min() >= 1e-3 and rho.max() <= 1.0
+    assert rho.std() > 0.05                                # far from the trivial uniform field
+    # zero weights: y = 0, uniform V, mu = ln(Vh / (V - rho_min) - 1) / k in closed form
+    r0, mu = init.sigmoid_projection(np.zeros(10), V, 1e-3)
+    assert np.abs(r0 - V).max() < 1e-12
+    assert abs(mu - np.log(0.45 / (V - 1e-3) - 1) / 15) < 1e-12
