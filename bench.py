@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--sample-n", type=int, default=16, help="cell size of the oracle's CPU sample")
     ap.add_argument("--sweeps", type=int, default=0, help="smoothing sweeps before/after coarse correction (0 = library default)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
+    ap.add_argument("--sym", default="none", choices=["none", "reflect3", "rotate3", "reflect6"],
+                    help="symmetry enforced on the sensitivity and the density every step")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "mixed"],
                     help="mixed: coarse-level stencils of the preconditioner stored in BF16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -198,7 +200,7 @@ def algorithmic_work(kc: str, n: int, sweeps: int = 1):
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("fine.cu", "dev_common.cuh", "homo_internal.cuh"):
+    for f in ("fine_gs.cu", "stencil.cuh", "dev_common.cuh"):
         with open(os.path.join(ROOT, "paper_2301_08911_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -261,6 +263,7 @@ def config_dict(args):
             "density": f"seeded blurred-noise inclusions (seed {args.seed}), exactly vf solid",
             "l2": "inputs larger than L2 (18 planes x n^3 fp32 per field)",
             "parallelism": "replicas (one cell per GPU, no collective)",
+            "symmetry": args.sym,
             "precision": ("FP32 storage and arithmetic; double-float displacement and CG correction"
                           if args.precision == "fp32" else
                           "FP32 arithmetic; coarse-level stencils stored in BF16 (symmetrised); "
@@ -322,7 +325,11 @@ def run_ours(args, rank, world, local):
         f, g = binding.objective(args.objective, C, state["it"], beta)
         hom.sensitivity(g, s)
         hom.filter(2.0, s, dc)
+        if args.sym != "none":
+            hom.symmetrize(args.sym, dc, dc)
         hom.update(dc, r, args.vf)
+        if args.sym != "none":
+            hom.symmetrize(args.sym, r, r)
         state["it"] += 1
         state["cg"].append(its)
         state["relres"].append(max(rel))

@@ -143,6 +143,46 @@ int homo_level_size(const homo_ctx* ctx, int level);
  *   in, out: device, N floats each; must not alias. 0 < radius <= 3.5. */
 int homo_filter(homo_ctx* ctx, double radius, const float* in, float* out);
 
+/* Sensitivity filter of the unfiltered variant (Sec. 5.3: the density is penalised
+ * directly, E = Emin + rho^p (E0 - Emin), and the sensitivity is filtered before the OC
+ * update). The paper names the step without its formula; this is the classic
+ * density-weighted mesh-independence filter with the same periodic cone weights:
+ *   out_e = sum_d w(d) rho_(e+d) dc_(e+d) / (max(gamma, rho_e) sum_d w(d)).
+ *   rho, dc, out: device, N floats each; out must alias neither rho nor dc.
+ *   0 < radius <= 3.5; 0 < gamma <= 1 (1e-3 is the usual choice). */
+int homo_filter_sensitivity(homo_ctx* ctx, double radius, const float* rho, const float* dc,
+                            double gamma, float* out);
+
+/* Trigonometric density initialisation (Sec. 6.2). At the element centres x (unit cell),
+ * with xb = R_q (x - (1/2, 1/2, 1/2)) and R_q the rotation of the quaternion q (scalar
+ * first, normalised here), the basis T = {cos, sin}(2 pi k xb_i), k = 1..nb, i = 0..2, in
+ * the order index 2 (3 (k-1) + i) + {0 cos, 1 sin}, is extended by the products T_a T_b,
+ * a <= b (row by row after T); y = sum of weights[j] times member j. Then
+ *   rho_e = clamp(rho_min + Vh / (1 + exp(-15 (y_e - mu))), rho_min, 1), Vh = min(1.5 V, 1),
+ * with mu found so that the mean density is V (bisection, 32 shifts per pass).
+ *   nb: 1..3; weights: host, nweights = 6 nb + 6 nb (6 nb + 1) / 2 (drawn in [-1, 1] by
+ *   the caller); q: host, 4 doubles, not all zero; 0 <= rho_min < volfrac < 1;
+ *   rho_out: device, N floats. Arithmetic in FP64 (a one-time setup step). Uses the
+ *   context's CG scratch; synchronises the stream. */
+int homo_trig_init(homo_ctx* ctx, int nb, const double q[4], const double* weights, int nweights,
+                   double volfrac, double rho_min, float* rho_out);
+
+/* Symmetry enforcement (Sec. 6.1): every element value becomes the average over its
+ * orbit under the chosen group of the cube, as the paper's loop does to the sensitivity
+ * before the OC update and to the density after it.
+ *   kind: HOMO_SYM_REFLECT3 - reflections in the mid-planes x, y, z = 1/2 (8 maps);
+ *         HOMO_SYM_ROTATE3  - rotations generated by quarter turns about the axes through
+ *                             the centre (24 maps);
+ *         HOMO_SYM_REFLECT6 - mid-plane reflections and reflections in the diagonal
+ *                             planes x = y, y = z, z = x (all 48 signed permutations).
+ *   in, out: device, N floats each; out may equal in (in-place).
+ * Orbit members receive bitwise-equal values when the orbit's values lie within a factor
+ * 2^29 of each other (FP64 sums of at most 48 FP32 values are then exact). */
+#define HOMO_SYM_REFLECT3 1
+#define HOMO_SYM_ROTATE3 2
+#define HOMO_SYM_REFLECT6 3
+int homo_symmetrize(homo_ctx* ctx, int kind, const float* in, float* out);
+
 /* Set the physical (filtered) density rho~ and derive E_e (Sec. 3.2). Values are
  * clamped to [0, 1]. rho: N floats, device (on_device = 1) or host (on_device = 0).
  * Marks loads and the multigrid hierarchy stale; the 6 displacement fields are kept

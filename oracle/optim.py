@@ -5,6 +5,7 @@ import numpy as np
 
 from .fem import homogenize, sensitivity
 from .filters import cone_filter
+from .symmetry import symmetrize
 
 
 def oc_update(rho: np.ndarray, dc: np.ndarray, volfrac: float, move: float = 0.05,
@@ -88,15 +89,20 @@ def optimization_iteration(rho: np.ndarray, n: int, volfrac: float, kind: str = 
                            iteration: int = 0, radius: float = 2.0, E0: float = 1.0,
                            nu: float = 0.3, p: float = 3.0, Emin: float = 1e-9,
                            move: float = 0.05, eta: float = 0.5, rho_min: float = 1e-3,
-                           method: str = "lu") -> dict:
+                           method: str = "lu", sym: str | None = None) -> dict:
     """One iteration of the loop of Sec. 5.2: filter -> SIMP -> 6 solves -> C^H -> f ->
-    sensitivity -> filter adjoint (the filter itself) -> OC update."""
+    sensitivity -> filter adjoint (the filter itself) -> [symmetrise the sensitivity] ->
+    OC update -> [symmetrise the density]; sym: None or a kind of Sec. 6.1."""
     rho_t = cone_filter(rho, n, radius)
     hom = homogenize(rho_t, n, E0, nu, p, Emin, method)
     f, g = objective(kind, hom["C"], iteration)
     s = sensitivity(rho_t, hom["q"], g, p, E0, Emin)
     dc = cone_filter(s, n, radius)
+    if sym:
+        dc = symmetrize(dc, n, sym)
     rho_new, lam, change = oc_update(rho, dc, volfrac, move, eta, rho_min)
+    if sym:
+        rho_new = symmetrize(rho_new, n, sym)
     out = dict(hom)
     out.update(rho_t=rho_t, f_obj=f, dfdC=g, s=s, dc=dc, rho_new=rho_new, lam=lam, change=change)
     return out

@@ -32,6 +32,7 @@ class HomoOpts(ctypes.Structure):
 
 SMOOTHERS = {"gs8": 0, "chebyshev": 1}
 PRECISIONS = {"fp32": 0, "mixed": 1}
+SYMMETRIES = {"reflect3": 1, "rotate3": 2, "reflect6": 3}
 
 
 # name -> (restype, argtypes), mirroring include/homo.h
@@ -47,6 +48,10 @@ SIGNATURES = {
     "homo_level_size": (ctypes.c_int, [_vp, ctypes.c_int]),
     "homo_filter": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp]),
     "homo_set_density": (ctypes.c_int, [_vp, _vp, ctypes.c_int]),
+    "homo_symmetrize": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "homo_trig_init": (ctypes.c_int, [_vp, ctypes.c_int, _c_double_p, _c_double_p, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, _vp]),
+    "homo_filter_sensitivity": (ctypes.c_int, [_vp, ctypes.c_double, _vp, _vp, ctypes.c_double, _vp]),
     "homo_solve_cases": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int, ctypes.c_int, _c_int_p, _c_double_p]),
     "homo_CH": (ctypes.c_int, [_vp, _c_double_p]),
     "homo_sensitivity": (ctypes.c_int, [_vp, _c_double_p, _vp]),
@@ -185,6 +190,22 @@ class Homogenization:
     # ---------------------------------------------------------------- hot path
     def filter(self, radius: float, inp, out):
         self._check(self.lib.homo_filter(self.h, radius, _vp(_ptr(inp)), _vp(_ptr(out))))
+
+    def filter_sensitivity(self, radius: float, rho, dc, out, gamma: float = 1e-3):
+        """Density-weighted sensitivity filter of the unfiltered variant (Sec. 5.3)."""
+        self._check(self.lib.homo_filter_sensitivity(self.h, radius, _vp(_ptr(rho)), _vp(_ptr(dc)), gamma,
+                                                     _vp(_ptr(out))))
+
+    def trig_init(self, nb: int, q, weights, volfrac: float, rho_out, rho_min: float = 1e-3):
+        """Trigonometric initial density (Sec. 6.2) into the device tensor rho_out."""
+        qa = (ctypes.c_double * 4)(*[float(v) for v in q])
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        wa = (ctypes.c_double * max(w.size, 1))(*w.tolist())
+        self._check(self.lib.homo_trig_init(self.h, nb, qa, wa, int(w.size), volfrac, rho_min, _vp(_ptr(rho_out))))
+
+    def symmetrize(self, kind: str, inp, out):
+        """Orbit averages of an element field under a cube symmetry (Sec. 6.1); out may be inp."""
+        self._check(self.lib.homo_symmetrize(self.h, SYMMETRIES[kind], _vp(_ptr(inp)), _vp(_ptr(out))))
 
     def set_density(self, rho):
         if isinstance(rho, np.ndarray):

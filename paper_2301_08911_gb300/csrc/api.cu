@@ -170,7 +170,10 @@ int ensure_hierarchy(homo_ctx* c) {
     KL(c, HOMO_KC_SETUP, 1, launch_fine_stencil(c, c->lev[0]));
   } else {
     KL(c, HOMO_KC_SETUP, 1, launch_level1_assemble(c, c->lev[1]));
-    for (int l = 1; l + 1 < c->nlev; ++l) KL(c, HOMO_KC_SETUP, 1, launch_galerkin(c->lev[l], c->lev[l + 1], c->stream));
+    // the fine CG vectors z and q are free while the hierarchy is built (18 N floats each;
+    // the intermediates of level 1 need 243 N / 16 and 243 N / 32)
+    for (int l = 1; l + 1 < c->nlev; ++l)
+      KL(c, HOMO_KC_SETUP, 3, launch_galerkin(c->lev[l], c->lev[l + 1], c->z, c->q, c->stream));
   }
   KL(c, HOMO_KC_SETUP, 3, launch_coarsest_setup(c));
   for (int l = 1; l + 1 < c->nlev; ++l)
@@ -552,6 +555,76 @@ int homo_filter(homo_ctx* ctx, double radius, const float* in, float* out) {
   if (build_filter_param(radius, fp) != HOMO_OK)
     return set_err(ctx, HOMO_EINVAL, "filter radius must be in (0, 3.5]");
   KL(ctx, HOMO_KC_FILTER, 1, launch_filter(fp, ctx->n, in, out, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_filter_sensitivity(homo_ctx* ctx, double radius, const float* rho, const float* dc,
+                            double gamma, float* out) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!valid_ptr(rho) || !valid_ptr(dc) || !valid_ptr(out) || out == rho || out == dc)
+    return set_err(ctx, HOMO_EINVAL, "filter_sensitivity: null or aliased buffers");
+  if (!(gamma > 0.0 && gamma <= 1.0)) return set_err(ctx, HOMO_EINVAL, "filter_sensitivity: gamma in (0, 1]");
+  FilterParam fp;
+  if (build_filter_param(radius, fp) != HOMO_OK)
+    return set_err(ctx, HOMO_EINVAL, "filter radius must be in (0, 3.5]");
+  KL(ctx, HOMO_KC_FILTER, 1,
+     launch_sensitivity_filter(fp, ctx->n, rho, dc, static_cast<float>(gamma), out, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_trig_init(homo_ctx* ctx, int nb, const double q[4], const double* weights, int nweights,
+                   double volfrac, double rho_min, float* rho_out) {
+  if (!ctx) return HOMO_EINVAL;
+  homo_ctx* c = ctx;
+  const int nt = 6 * nb;
+  if (nb < 1 || nb > 3 || !q || !weights || !valid_ptr(rho_out) || nweights != nt + nt * (nt + 1) / 2)
+    return set_err(c, HOMO_EINVAL, "trig_init: 1 <= nb <= 3 and one weight per member of Q_n required");
+  const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (!(qn > 0.0) || !(rho_min >= 0.0 && rho_min < 1.0) || !(volfrac > rho_min && volfrac < 1.0))
+    return set_err(c, HOMO_EINVAL, "trig_init: nonzero quaternion, 0 <= rho_min < volfrac < 1 required");
+  TrigParam tp{};
+  const double w = q[0] / qn, x = q[1] / qn, y = q[2] / qn, z = q[3] / qn;
+  const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                       2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                       2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+  for (int i = 0; i < 9; ++i) tp.R[i] = R[i];
+  tp.nb = nb;
+  double wabs = 0.0;
+  for (int i = 0; i < nweights; ++i) {
+    tp.w[i] = weights[i];
+    wabs += std::fabs(weights[i]);
+  }
+  // y in the fine vector z (18 N floats hold N doubles; z is free outside a solve)
+  double* yv = reinterpret_cast<double*>(c->z);
+  KL(c, HOMO_KC_OTHER, 1, launch_trig_basis(tp, c->n, yv, c->stream));
+  const double k = 15.0, Vh = std::min(1.5 * volfrac, 1.0);
+  // |y| <= sum |w|; the mean density falls from rho_min + Vh to rho_min across the bracket
+  double lo = -wabs - 60.0 / k, hi = wabs + 60.0 / k;
+  const double target = volfrac * static_cast<double>(c->N);
+  for (int pass = 0; pass < 12 && hi - lo > 1e-13 * (1.0 + std::fabs(lo)); ++pass) {
+    const double dmu = (hi - lo) / (kTrigCand - 1);
+    int g = 0;
+    KL(c, HOMO_KC_OTHER, 1, launch_trig_volume(yv, c->N, lo, dmu, k, Vh, rho_min, c->part, &g, c->stream));
+    KL(c, HOMO_KC_OTHER, 1, launch_sum_partials(c->part, g, kTrigCand, c->scal + S_OC, c->stream));
+    RET(sync_read(c, S_OC, kTrigCand));
+    int last = 0;   // last candidate whose mean is still above the target
+    for (int cnd = 0; cnd < kTrigCand; ++cnd)
+      if (c->hscal[S_OC + cnd] > target) last = cnd;
+    const double nlo = lo + last * dmu;
+    hi = std::min(hi, nlo + dmu);
+    lo = nlo;
+  }
+  KL(c, HOMO_KC_OTHER, 1, launch_trig_project(yv, c->N, 0.5 * (lo + hi), k, Vh, rho_min, rho_out, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return HOMO_OK;
+}
+
+int homo_symmetrize(homo_ctx* ctx, int kind, const float* in, float* out) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!valid_ptr(in) || !valid_ptr(out)) return set_err(ctx, HOMO_EINVAL, "symmetrize: null buffer");
+  SymParam sp;
+  if (build_sym_param(kind, sp) != HOMO_OK) return set_err(ctx, HOMO_EINVAL, "symmetrize: unknown kind");
+  KL(ctx, HOMO_KC_FILTER, 1, launch_symmetrize(sp, ctx->n, in, out, ctx->stream));
   return HOMO_OK;
 }
 

@@ -66,56 +66,64 @@ __global__ void __launch_bounds__(128) k_level1(const __grid_constant__ BfParam 
   }
 }
 
-// Galerkin product R K I on vertex stencils (Sec. 3.3): the block between coarse vertex V
-// and V + d is sum over fine a near 2V and b near 2(V+d), |b - a| <= 1, of
-// w(a - 2V) w(b - 2V - 2d) K_(a, b - a), with tent weights w(e) = prod (1 - |e_k|/2).
-// One thread per (coarse vertex, d); consecutive threads take consecutive stencil
-// positions so the stores are coalesced.
-__global__ void __launch_bounds__(256) k_galerkin(const float* __restrict__ sf, int nf, bool cbf,
-                                                  float* __restrict__ sc, int nc, bool cbc) {
-  const size_t Nf = static_cast<size_t>(nf) * nf * nf;
-  const size_t Nc = static_cast<size_t>(nc) * nc * nc;
-  const size_t total = 27 * Nc;
+// One axis of the Galerkin product R K I (Eq. 17-18 on coarse levels). The trilinear
+// transfers are tensor products of the 1-D linear interpolation, so R K I factors into
+// three one-axis coarsenings, each a 27-point block stencil again. Coarsening axis `ax`
+// of a stencil S on an (mx, my, mz) grid: for output vertex V and output offset d,
+//   S'(V, d) = sum over a, e in {-1,0,1} with |2 d_ax + e - a| <= 1 of
+//              w(a) w(e) S(V with x_ax -> 2 V_ax + a, d with d_ax -> 2 d_ax + e - a),
+// w(t) = 1 - |t|/2: 7 pairs when d_ax = 0, 3 when d_ax = +-1. src_cb / dst_cb: the grid
+// is cubic and its stencil planes are colour-blocked (a level's own layout); otherwise
+// x-fastest. Thread per (d, output vertex).
+template <int ax>
+__global__ void __launch_bounds__(256) k_galerkin_axis(const float* __restrict__ src, int mx, int my, int mz,
+                                                       bool src_cb, float* __restrict__ dst, bool dst_cb) {
+  const int ox = ax == 0 ? mx / 2 : mx, oy = ax == 1 ? my / 2 : my, oz = ax == 2 ? mz / 2 : mz;
+  const size_t Nin = static_cast<size_t>(mx) * my * mz;
+  const size_t Nout = static_cast<size_t>(ox) * oy * oz;
+  const size_t total = 27 * Nout;
   for (size_t it = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; it < total;
        it += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int d = static_cast<int>(it / Nc);
-    const size_t p = it - static_cast<size_t>(d) * Nc;
-    int X, Y, Z;
-    vertex_of_pos(p, nc, cbc, X, Y, Z);
+    const int d = static_cast<int>(it / Nout);
+    const size_t p = it - static_cast<size_t>(d) * Nout;
+    int V[3];
+    if (dst_cb) {
+      vertex_of_pos(p, ox, true, V[0], V[1], V[2]);
+    } else {
+      const unsigned q = static_cast<unsigned>(p) / static_cast<unsigned>(ox);
+      V[0] = static_cast<int>(static_cast<unsigned>(p) - q * static_cast<unsigned>(ox));
+      V[2] = static_cast<int>(q / static_cast<unsigned>(oy));
+      V[1] = static_cast<int>(q - static_cast<unsigned>(V[2]) * static_cast<unsigned>(oy));
+    }
     const int D[3] = {d % 3 - 1, (d / 3) % 3 - 1, d / 9 - 1};
+    const int m_ax = ax == 0 ? mx : (ax == 1 ? my : mz);
     float A[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) A[q] = 0.f;
-    for (int az = -1; az <= 1; ++az)
-      for (int ay = -1; ay <= 1; ++ay)
-        for (int ax = -1; ax <= 1; ++ax) {
-          const float wa = (1.f - 0.5f * abs(ax)) * (1.f - 0.5f * abs(ay)) * (1.f - 0.5f * abs(az));
-          const int fx = ((2 * X + ax) % nf + nf) % nf, fy = ((2 * Y + ay) % nf + nf) % nf,
-                    fz = ((2 * Z + az) % nf + nf) % nf;
-          const size_t pa = stencil_pos(fx, fy, fz, nf, cbf);
-          const int a3[3] = {ax, ay, az};
-          // b - 2V = 2D + e, e in {-1,0,1}; need |b - a| <= 1
-          for (int ez = -1; ez <= 1; ++ez) {
-            const int bz = 2 * D[2] + ez - a3[2];
-            if (bz < -1 || bz > 1) continue;
-            for (int ey = -1; ey <= 1; ++ey) {
-              const int by = 2 * D[1] + ey - a3[1];
-              if (by < -1 || by > 1) continue;
-              for (int ex = -1; ex <= 1; ++ex) {
-                const int bx = 2 * D[0] + ex - a3[0];
-                if (bx < -1 || bx > 1) continue;
-                const float wb = (1.f - 0.5f * abs(ex)) * (1.f - 0.5f * abs(ey)) * (1.f - 0.5f * abs(ez));
-                const float ww = wa * wb;
-                const int dd = (bx + 1) + 3 * (by + 1) + 9 * (bz + 1);
 #pragma unroll
-                for (int q = 0; q < 9; ++q)
-                  A[q] = fmaf(ww, __ldg(sf + static_cast<size_t>(9 * dd + q) * Nf + pa), A[q]);
-              }
-            }
-          }
-        }
+    for (int a = -1; a <= 1; ++a) {
+      int F[3] = {V[0], V[1], V[2]};
+      int fa = 2 * V[ax] + a;
+      fa = fa < 0 ? fa + m_ax : (fa >= m_ax ? fa - m_ax : fa);
+      F[ax] = fa;
+      const size_t pin = src_cb ? stencil_pos(F[0], F[1], F[2], mx, true)
+                                : static_cast<size_t>(F[0]) + static_cast<size_t>(mx) *
+                                      (F[1] + static_cast<size_t>(my) * F[2]);
+      const float wa = a ? 0.5f : 1.f;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) sc[static_cast<size_t>(9 * d + q) * Nc + p] = A[q];
+      for (int e = -1; e <= 1; ++e) {
+        const int bax = 2 * D[ax] + e - a;
+        if (bax < -1 || bax > 1) continue;
+        int B[3] = {D[0], D[1], D[2]};
+        B[ax] = bax;
+        const int dd = (B[0] + 1) + 3 * (B[1] + 1) + 9 * (B[2] + 1);
+        const float ww = wa * (e ? 0.5f : 1.f);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) A[q] = fmaf(ww, __ldg(src + static_cast<size_t>(9 * dd + q) * Nin + pin), A[q]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 9; ++q) dst[static_cast<size_t>(9 * d + q) * Nout + p] = A[q];   // p: output position
   }
 }
 
@@ -551,9 +559,14 @@ cudaError_t launch_level1_assemble(const homo_ctx* c, const Level& L1) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, cudaStream_t s) {
-  k_galerkin<<<grid_for(27 * Lc.N, 256), 256, 0, s>>>(Lf.st, Lf.n, Lf.colour_blocked, Lc.st, Lc.n,
-                                                     Lc.colour_blocked);
+cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, float* tmp1, float* tmp2, cudaStream_t s) {
+  const int n = Lf.n, h = n / 2;
+  if (Lc.n != h || !Lf.colour_blocked) return cudaErrorInvalidValue;
+  const size_t n1 = static_cast<size_t>(h) * n * n, n2 = static_cast<size_t>(h) * h * n;
+  // x: level stencil -> (h, n, n) in tmp1; y: -> (h, h, n) in tmp2; z: -> the coarse level
+  k_galerkin_axis<0><<<grid_for(27 * n1, 256), 256, 0, s>>>(Lf.st, n, n, n, true, tmp1, false);
+  k_galerkin_axis<1><<<grid_for(27 * n2, 256), 256, 0, s>>>(tmp1, h, n, n, false, tmp2, false);
+  k_galerkin_axis<2><<<grid_for(27 * Lc.N, 256), 256, 0, s>>>(tmp2, h, h, n, false, Lc.st, Lc.colour_blocked);
   return cudaGetLastError();
 }
 

@@ -11,119 +11,11 @@
 #include <string>
 
 #include "dev_common.cuh"
+#include "stencil.cuh"
 
 namespace homo {
 
 namespace {
-
-__device__ __forceinline__ void load_E8(const float* __restrict__ E, const Nb& nb, float (&Et)[8]) {
-#pragma unroll
-  for (int t = 0; t < 8; ++t) Et[t] = __ldg(E + nb.X[t & 1] + nb.Y[(t >> 1) & 1] + nb.Z[t >> 2]);
-}
-
-// 3x3 block A_d for neighbour offset (dx,dy,dz); all index arithmetic folds at compile
-// time once the callers' loops are unrolled.
-__device__ __forceinline__ void nb_block(const KeParam& K, const float (&Et)[8], int dx, int dy,
-                                         int dz, float (&A)[9]) {
-#pragma unroll
-  for (int q = 0; q < 9; ++q) A[q] = 0.f;
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int ja = dx + 1 - (t & 1), jb = dy + 1 - ((t >> 1) & 1), jc = dz + 1 - (t >> 2);
-    if (ja < 0 || ja > 1 || jb < 0 || jb > 1 || jc < 0 || jc > 1) continue;
-    const int j = ja + 2 * jb + 4 * jc, row = 7 - t;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        A[3 * r + c] = fmaf(Et[t], K.k[(3 * row + r) * 24 + 3 * j + c], A[3 * r + c]);
-  }
-}
-
-// Solve the SPD 3x3 system S y = b for NC right-hand sides (LDL^T, FP32).
-template <int NC>
-__device__ __forceinline__ void solve3xn(const float (&S)[9], float (&b)[3 * NC]) {
-  const float d0 = S[0];
-  const float l10 = S[3] / d0, l20 = S[6] / d0;
-  const float d1 = S[4] - l10 * S[1];
-  const float l21 = (S[7] - l20 * S[1]) / d1;
-  const float d2 = S[8] - l20 * S[2] - l21 * (S[5] - l10 * S[2]);
-  const float i0 = 1.f / d0, i1 = 1.f / d1, i2 = 1.f / d2;
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    float y0 = b[3 * c], y1 = b[3 * c + 1], y2 = b[3 * c + 2];
-    y1 -= l10 * y0;
-    y2 -= l20 * y0 + l21 * y1;
-    float x2 = y2 * i2;
-    float x1 = y1 * i1 - l21 * x2;
-    float x0 = y0 * i0 - l10 * x1 - l20 * x2;
-    b[3 * c] = x0;
-    b[3 * c + 1] = x1;
-    b[3 * c + 2] = x2;
-  }
-}
-
-__device__ __forceinline__ void solve3x6(const float (&S)[9], float (&b)[18]) { solve3xn<kCases>(S, b); }
-
-// One colour pass of 8-colour block Gauss-Seidel (Eq. 15-16): for every vertex v of
-// the colour, S_v u_v = f_v - M_v with S_v = A_0 and M_v = sum_(d != 0) A_d u_(v+d).
-// The neighbour v + d has colour (colour XOR oddness-mask of d), never the pass's own
-// colour, so its value is not written during the pass (read through the read-only
-// path). first != 0: first sweep from u = 0 in colour order 0..7, where neighbours of a
-// higher colour still hold zero and are skipped (u need not be cleared beforehand).
-// The load cases are split over blockIdx.y in groups of kGsCases: the blocks A_d are
-// rebuilt per group, which keeps registers low and puts more loads in flight.
-constexpr int kGsCases = 3;
-
-__global__ void __launch_bounds__(256, 4) k_fine_gs(const __grid_constant__ KeParam K,
-                                                 const float* __restrict__ E,
-                                                 const float* __restrict__ f,
-                                                 float* __restrict__ u, int n, int colour,
-                                                 int first, const double* __restrict__ fmean) {
-  const size_t N = static_cast<size_t>(n) * n * n;
-  const int h = n >> 1;
-  const size_t Nh = static_cast<size_t>(h) * h * h;
-  const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
-  const int q0 = 3 * kGsCases * blockIdx.y;                // first plane of the case group
-  for (size_t m = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < Nh;
-       m += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    int i, j, k;
-    decode3(static_cast<unsigned>(m), static_cast<unsigned>(h), i, j, k);
-    const int x = 2 * i + cx, y = 2 * j + cy, z = 2 * k + cz;
-    const size_t v = static_cast<size_t>(x) + static_cast<size_t>(n) * (y + static_cast<size_t>(n) * z);
-    const Nb nb = make_nb(x, y, z, n);
-    float Et[8];
-    load_E8(E, nb, Et);
-    float rhs[3 * kGsCases];
-#pragma unroll
-    for (int q = 0; q < 3 * kGsCases; ++q)
-      rhs[q] = __ldg(f + (q0 + q) * N + v) - (fmean ? static_cast<float>(fmean[q0 + q]) : 0.f);
-#pragma unroll
-    for (int d = 0; d < 27; ++d) {
-      if (d == 13) continue;
-      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
-      const int odd = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
-      if (first && (colour ^ odd) > colour) continue;
-      float A[9];
-      nb_block(K, Et, dx, dy, dz, A);
-      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
-      const float* ur = u + q0 * N + w;
-#pragma unroll
-      for (int c = 0; c < kGsCases; ++c) {
-        const float u0 = __ldg(ur + (3 * c) * N), u1 = __ldg(ur + (3 * c + 1) * N),
-                    u2 = __ldg(ur + (3 * c + 2) * N);
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-          rhs[3 * c + r] = fmaf(-A[3 * r + 2], u2, fmaf(-A[3 * r + 1], u1, fmaf(-A[3 * r], u0, rhs[3 * c + r])));
-      }
-    }
-    float S[9];
-    nb_block(K, Et, 0, 0, 0, S);
-    solve3xn<kGsCases>(S, rhs);
-#pragma unroll
-    for (int q = 0; q < 3 * kGsCases; ++q) u[(q0 + q) * N + v] = rhs[q];
-  }
-}
 
 // Macro-strain loads in vertex form (Eq. 11): f_(i,v) = sum_t E_t (K0 chi_i)[7 - t].
 // In a uniform medium the 8 element forces at a vertex cancel exactly (sum_t (K0
@@ -180,8 +72,8 @@ __global__ void __launch_bounds__(128) k_fine_true_residual(const __grid_constan
   for (int c = 0; c < kCases + kPlanes; ++c) red[c] = 0.f;
   for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
        v += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
-              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
+    int x, y, z;
+    decode3(static_cast<unsigned>(v), static_cast<unsigned>(n), x, y, z);
     const Nb nb = make_nb(x, y, z, n);
     float Et[8];
     load_E8(E, nb, Et);
@@ -308,14 +200,25 @@ struct ElemParam {
   float invN;
 };
 
-constexpr int kElemBlock = 128;
-constexpr int kElemStride = 165;   // 144 w values + 21 products per thread row (odd: bank spread)
+constexpr int kElemCases = kCases;            // one warp per load case
+constexpr int kElemBlock = 32 * kElemCases;   // 32 elements x 6 cases
+constexpr int kElemPad = 25;                  // w row stride in shared memory (bank spread)
+
+// Pair slot of (i, j) in the row-major upper triangle of the 6x6 C^H (i <= j).
+__host__ __device__ constexpr int pair_slot(int i, int j) {
+  return i <= j ? i * kCases - i * (i - 1) / 2 + (j - i) : j * kCases - j * (j - 1) / 2 + (i - j);
+}
 
 // Per element q_ij = w_i^T K0 w_j, w_i = chi_i - (u_i - u_i at local vertex 0): the
 // summand of Eq. 7 (subtracting the element's own translation leaves K0 w unchanged and
 // keeps FP32 round-off independent of the field's magnitude, cf. Sec. 4.2 "relative
-// coordinate"). MODE 0: block partial sums of E_e q_ij (21 values, Kahan-compensated
-// per thread). MODE 1: sensitivity (Eq. 8-9) p rho^(p-1) dE sum_ij g_ij q_ij / N.
+// coordinate"). Six threads per element, one per load case i and each in its own warp,
+// so a warp's loads cover 32 consecutive elements: thread i gathers w_i (both parts of
+// the double-float field), forms y_i = K0 w_i and the products q_ij = y_i . w_j of the
+// pairs dealt to it (q_ij = q_ji: the diagonal, i+1, i+2 and, for i < 3, i+3 mod 6, so
+// 3 or 4 each), reading the other w_j from shared memory.
+// MODE 0: block partial sums of E_e q_ij (21 values, Kahan-compensated per thread).
+// MODE 1: sensitivity (Eq. 8-9) p rho^(p-1) dE sum_ij g_ij q_ij / N.
 template <int MODE>
 __global__ void __launch_bounds__(kElemBlock) k_fine_elem(const __grid_constant__ KeParam K,
                                                           const __grid_constant__ ChiParam X,
@@ -326,70 +229,105 @@ __global__ void __launch_bounds__(kElemBlock) k_fine_elem(const __grid_constant_
                                                           const float* __restrict__ ulo, int n,
                                                           float* __restrict__ sens,
                                                           double* __restrict__ part) {
-  extern __shared__ float wsh[];
-  float* w = wsh + threadIdx.x * kElemStride;
+  __shared__ float ws[kElemCases][32][kElemPad];
+  __shared__ float sp[kElemCases][32];
+  __shared__ double sacc[21];
+  const int lane = threadIdx.x & 31, i = threadIdx.x >> 5;   // element slot, load case
   const size_t N = static_cast<size_t>(n) * n * n;
-  float cs[21], cc[21];
+  const int npair = i < 3 ? 4 : 3;
+  int jp[4], slot[4];
 #pragma unroll
-  for (int k = 0; k < 21; ++k) cs[k] = cc[k] = 0.f;
-  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
-       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(e % n), y = static_cast<int>((e / n) % n),
-              z = static_cast<int>(e / (static_cast<size_t>(n) * n));
-    const int xs[2] = {x, x == n - 1 ? 0 : x + 1};
-    const int ys[2] = {y * n, (y == n - 1 ? 0 : y + 1) * n};
-    const int zs[2] = {z * n * n, (z == n - 1 ? 0 : z + 1) * n * n};
+  for (int k = 0; k < 4; ++k) {
+    jp[k] = (i + k) % kCases;
+    slot[k] = pair_slot(i, jp[k]);
+  }
+  float cs[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (size_t e0 = static_cast<size_t>(blockIdx.x) * 32; e0 < N; e0 += static_cast<size_t>(gridDim.x) * 32) {
+    const size_t e = e0 + lane;
+    const bool live = e < N;
+    float w[24];
+    if (live) {
+      int x, y, z;
+      decode3(static_cast<unsigned>(e), static_cast<unsigned>(n), x, y, z);
+      const int xs[2] = {x, x == n - 1 ? 0 : x + 1};
+      const int ys[2] = {y * n, (y == n - 1 ? 0 : y + 1) * n};
+      const int zs[2] = {z * n * n, (z == n - 1 ? 0 : z + 1) * n * n};
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) {
-      const float* uq = u + static_cast<size_t>(q) * N;
-      const float* lq = ulo + static_cast<size_t>(q) * N;
-      const float h0 = __ldg(uq + e), l0 = __ldg(lq + e);
-      const int c = q / 3, k = q % 3;
+      for (int k = 0; k < 3; ++k) {
+        const float* uq = u + static_cast<size_t>(3 * i + k) * N;
+        const float* lq = ulo + static_cast<size_t>(3 * i + k) * N;
+        const float h0 = __ldg(uq + e), l0 = __ldg(lq + e);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const size_t vj = static_cast<size_t>(xs[j & 1] + ys[(j >> 1) & 1] + zs[j >> 2]);
-        const float du = (__ldg(uq + vj) - h0) + (__ldg(lq + vj) - l0);
-        w[c * 24 + 3 * j + k] = X.chi[c][3 * j + k] - du;
-      }
-    }
-    float* q = w + 144;   // 21 products, (i, j >= i) row-major
-#pragma unroll 1
-    for (int i = 0, idx = 0; i < kCases; ++i) {
-      float yv[24];
-#pragma unroll
-      for (int r = 0; r < 24; ++r) yv[r] = 0.f;
-#pragma unroll
-      for (int k = 0; k < 24; ++k) {
-        const float wk = w[i * 24 + k];
-#pragma unroll
-        for (int r = 0; r < 24; ++r) yv[r] = fmaf(K.k[r * 24 + k], wk, yv[r]);
-      }
-#pragma unroll 1
-      for (int j = i; j < kCases; ++j, ++idx) {
-        float s = 0.f;
-#pragma unroll
-        for (int k = 0; k < 24; ++k) s = fmaf(yv[k], w[j * 24 + k], s);
-        q[idx] = s;
-      }
-    }
-    if (MODE == 0) {
-      const float Ee = __ldg(E + e);
-#pragma unroll
-      for (int k = 0; k < 21; ++k) {   // Kahan summation of E_e q_e,k
-        const float yk = fmaf(Ee, q[k], -cc[k]);
-        const float t = cs[k] + yk;
-        cc[k] = (t - cs[k]) - yk;
-        cs[k] = t;
+        for (int j = 0; j < 8; ++j) {
+          const size_t vj = static_cast<size_t>(xs[j & 1] + ys[(j >> 1) & 1] + zs[j >> 2]);
+          const float du = (__ldg(uq + vj) - h0) + (__ldg(lq + vj) - l0);
+          w[3 * j + k] = X.chi[i][3 * j + k] - du;
+        }
       }
     } else {
-      float s = 0.f;
 #pragma unroll
-      for (int k = 0; k < 21; ++k) s = fmaf(P.gsym[k], q[k], s);
+      for (int r = 0; r < 24; ++r) w[r] = 0.f;
+    }
+#pragma unroll
+    for (int r = 0; r < 24; ++r) ws[i][lane][r] = w[r];
+    __syncthreads();
+    float yv[24];
+#pragma unroll
+    for (int r = 0; r < 24; ++r) yv[r] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 24; ++k) {
+#pragma unroll
+      for (int r = 0; r < 24; ++r) yv[r] = fmaf(K.k[r * 24 + k], w[k], yv[r]);
+    }
+    float q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float sdot = 0.f;
+      if (k < npair) {
+        const float* wj = ws[jp[k]][lane];
+#pragma unroll
+        for (int r = 0; r < 24; ++r) sdot = fmaf(yv[r], wj[r], sdot);
+      }
+      q[k] = sdot;
+    }
+    if (MODE == 0) {
+      if (live) {
+        const float Ee = __ldg(E + e);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {   // Kahan summation of E_e q_e,k
+          const float yk = fmaf(Ee, q[k], -cc[k]);
+          const float t = cs[k] + yk;
+          cc[k] = (t - cs[k]) - yk;
+          cs[k] = t;
+        }
+      }
+    } else {
+      float sg = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) sg = fmaf(k < npair ? P.gsym[slot[k]] : 0.f, q[k], sg);
+      sp[i][lane] = sg;
+    }
+    __syncthreads();
+    if (MODE == 1 && i == 0 && live) {
+      float sg = 0.f;
+#pragma unroll
+      for (int c = 0; c < kElemCases; ++c) sg += sp[c][lane];
       const float r = __ldg(rho + e);
-      sens[e] = P.p * powf(r, P.p - 1.f) * P.dE * s * P.invN;
+      sens[e] = P.p * powf(r, P.p - 1.f) * P.dE * sg * P.invN;
     }
   }
-  if (MODE == 0) block_sum_store<21>(cs, part);
+  if (MODE == 0) {
+    // each pair slot belongs to exactly one warp: reduce the warp's 32 sums per slot
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      float v = cs[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0 && k < npair) sacc[slot[k]] = static_cast<double>(v);
+    }
+    __syncthreads();
+    if (threadIdx.x < 21) part[static_cast<size_t>(blockIdx.x) * 21 + threadIdx.x] = sacc[threadIdx.x];
+  }
 }
 
 }  // namespace
@@ -433,13 +371,6 @@ cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float*
   return launch_fine_tiled(c, 3, u, b, out, nullptr, grid_out, bmean);
 }
 
-cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first,
-                           const double* fmean) {
-  const size_t h = static_cast<size_t>(c->n / 2);
-  const dim3 grid(grid_for(h * h * h, 256), kCases / kGsCases);
-  k_fine_gs<<<grid, 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour, first, fmean);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, float* sens,
                              double* part, int* grid_out) {
@@ -453,19 +384,14 @@ cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, flo
   P.p = static_cast<float>(c->p);
   P.dE = static_cast<float>(c->E0 - c->Emin);
   P.invN = static_cast<float>(1.0 / static_cast<double>(c->N));
-  const int g = grid_for(c->N, kElemBlock);
+  const int g = grid_for((c->N + 31) / 32, 1);   // one block per 32 elements, capped
   if (grid_out) *grid_out = g;
-  const size_t shm = static_cast<size_t>(kElemBlock) * kElemStride * sizeof(float);
-  cudaError_t ae = cudaFuncSetAttribute(mode == 0 ? k_fine_elem<0> : k_fine_elem<1>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        static_cast<int>(shm));
-  if (ae != cudaSuccess) return ae;
   if (mode == 0)
-    k_fine_elem<0><<<g, kElemBlock, shm, c->stream>>>(c->ke, c->chi, P, c->E, c->rho, c->u, c->ulo,
-                                                     c->n, sens, part);
+    k_fine_elem<0><<<g, kElemBlock, 0, c->stream>>>(c->ke, c->chi, P, c->E, c->rho, c->u, c->ulo,
+                                                   c->n, sens, part);
   else
-    k_fine_elem<1><<<g, kElemBlock, shm, c->stream>>>(c->ke, c->chi, P, c->E, c->rho, c->u, c->ulo,
-                                                     c->n, sens, part);
+    k_fine_elem<1><<<g, kElemBlock, 0, c->stream>>>(c->ke, c->chi, P, c->E, c->rho, c->u, c->ulo,
+                                                   c->n, sens, part);
   return cudaGetLastError();
 }
 
@@ -487,15 +413,20 @@ static __device__ __align__(256) double g_noalloc_scratch[(kNoAllocBlocks + 1) *
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[256] = {};   // device address of g_noalloc_scratch, per device
 
-// Same element arithmetic as the C^H mode of k_fine_elem; ulo may be null (read as 0).
-__global__ void __launch_bounds__(kElemBlock) k_ch_noalloc(const __grid_constant__ KeParam K,
+// Thread per element, its 144 w values and 21 products in a shared-memory row.
+constexpr int kNoAllocElemBlock = 128;
+constexpr int kNoAllocStride = 165;   // 144 w values + 21 products per thread row (odd: bank spread)
+
+// The element arithmetic of Eq. 7 (w_i = chi_i - relative displacement, q_ij = w_i^T K0
+// w_j, Kahan sums of E_e q_ij) with one thread per element; ulo may be null (read as 0).
+__global__ void __launch_bounds__(kNoAllocElemBlock) k_ch_noalloc(const __grid_constant__ KeParam K,
                                                            const __grid_constant__ ChiParam X,
                                                            const float* __restrict__ E,
                                                            const float* __restrict__ u,
                                                            const float* __restrict__ ulo, int n,
                                                            double* __restrict__ scratch) {
   extern __shared__ float wsh[];
-  float* w = wsh + threadIdx.x * kElemStride;
+  float* w = wsh + threadIdx.x * kNoAllocStride;
   const size_t N = static_cast<size_t>(n) * n * n;
   float cs[21], cc[21];
 #pragma unroll
@@ -602,12 +533,12 @@ extern "C" int homo_CH_noalloc(int n, double nu, const float* E, const float* u,
   ChiParam chi;
   build_element_matrix(nu, ke, ld, chi);
   const size_t N = static_cast<size_t>(n) * n * n;
-  size_t blocks = (N + kElemBlock - 1) / kElemBlock;
+  size_t blocks = (N + kNoAllocElemBlock - 1) / kNoAllocElemBlock;
   if (blocks > static_cast<size_t>(kNoAllocBlocks)) blocks = kNoAllocBlocks;
-  const size_t shm = static_cast<size_t>(kElemBlock) * kElemStride * sizeof(float);
+  const size_t shm = static_cast<size_t>(kNoAllocElemBlock) * kNoAllocStride * sizeof(float);
   e = cudaFuncSetAttribute(k_ch_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(shm));
   if (e == cudaSuccess) {
-    k_ch_noalloc<<<static_cast<int>(blocks), kElemBlock, shm, s>>>(ke, chi, E, u, ulo, n, scratch);
+    k_ch_noalloc<<<static_cast<int>(blocks), kNoAllocElemBlock, shm, s>>>(ke, chi, E, u, ulo, n, scratch);
     k_ch_noalloc_total<<<1, 32, 0, s>>>(scratch, static_cast<int>(blocks));
     e = cudaGetLastError();
   }

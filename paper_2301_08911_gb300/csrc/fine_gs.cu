@@ -1,0 +1,78 @@
+// One colour pass of the finest-level 8-colour block Gauss-Seidel smoother (Eq. 15-16).
+#include "stencil.cuh"
+
+namespace homo {
+
+namespace {
+
+// One colour pass of 8-colour block Gauss-Seidel (Eq. 15-16): for every vertex v of
+// the colour, S_v u_v = f_v - M_v with S_v = A_0 and M_v = sum_(d != 0) A_d u_(v+d).
+// The neighbour v + d has colour (colour XOR oddness-mask of d), never the pass's own
+// colour, so its value is not written during the pass (read through the read-only
+// path). first != 0: first sweep from u = 0 in colour order 0..7, where neighbours of a
+// higher colour still hold zero and are skipped (u need not be cleared beforehand).
+// The load cases are split over blockIdx.y in groups of kGsCases: the blocks A_d are
+// rebuilt per group, which keeps registers low and puts more loads in flight.
+constexpr int kGsCases = 3;
+
+__global__ void __launch_bounds__(256, 4) k_fine_gs(const __grid_constant__ KeParam K,
+                                                 const float* __restrict__ E,
+                                                 const float* __restrict__ f,
+                                                 float* __restrict__ u, int n, int colour,
+                                                 int first, const double* __restrict__ fmean) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  const int h = n >> 1;
+  const size_t Nh = static_cast<size_t>(h) * h * h;
+  const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
+  const int q0 = 3 * kGsCases * blockIdx.y;                // first plane of the case group
+  for (size_t m = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; m < Nh;
+       m += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int i, j, k;
+    decode3(static_cast<unsigned>(m), static_cast<unsigned>(h), i, j, k);
+    const int x = 2 * i + cx, y = 2 * j + cy, z = 2 * k + cz;
+    const size_t v = static_cast<size_t>(x) + static_cast<size_t>(n) * (y + static_cast<size_t>(n) * z);
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    float rhs[3 * kGsCases];
+#pragma unroll
+    for (int q = 0; q < 3 * kGsCases; ++q)
+      rhs[q] = __ldg(f + (q0 + q) * N + v) - (fmean ? static_cast<float>(fmean[q0 + q]) : 0.f);
+#pragma unroll
+    for (int d = 0; d < 27; ++d) {
+      if (d == 13) continue;
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const int odd = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+      if (first && (colour ^ odd) > colour) continue;
+      float A[9];
+      nb_block(K, Et, dx, dy, dz, A);
+      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+      const float* ur = u + q0 * N + w;
+#pragma unroll
+      for (int c = 0; c < kGsCases; ++c) {
+        const float u0 = __ldg(ur + (3 * c) * N), u1 = __ldg(ur + (3 * c + 1) * N),
+                    u2 = __ldg(ur + (3 * c + 2) * N);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          rhs[3 * c + r] = fmaf(-A[3 * r + 2], u2, fmaf(-A[3 * r + 1], u1, fmaf(-A[3 * r], u0, rhs[3 * c + r])));
+      }
+    }
+    float S[9];
+    nb_block(K, Et, 0, 0, 0, S);
+    solve3xn<kGsCases>(S, rhs);
+#pragma unroll
+    for (int q = 0; q < 3 * kGsCases; ++q) u[(q0 + q) * N + v] = rhs[q];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first,
+                           const double* fmean) {
+  const size_t h = static_cast<size_t>(c->n / 2);
+  const dim3 grid(grid_for(h * h * h, 256), kCases / kGsCases);
+  k_fine_gs<<<grid, 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour, first, fmean);
+  return cudaGetLastError();
+}
+
+}  // namespace homo

@@ -54,6 +54,25 @@ struct FilterParam {
   float w[343];
 };
 
+// Cube symmetry group (Sec. 6.1) as signed axis permutations: the image of element
+// (i0, i1, i2) has index j_k = i_perm[k], mirrored to n-1-j_k when bit k of flip is set.
+struct SymParam {
+  int count;
+  unsigned char perm[48][3];
+  unsigned char flip[48];
+};
+
+// Trigonometric initialisation (Sec. 6.2): rotation, basis size and the weights of
+// Q_n (at most nb = 3: 18 + 171 weights).
+constexpr int kTrigMaxT = 18;
+constexpr int kTrigMaxW = kTrigMaxT + kTrigMaxT * (kTrigMaxT + 1) / 2;
+struct TrigParam {
+  double R[9];
+  int nb;
+  double w[kTrigMaxW];
+};
+constexpr int kTrigCand = 32;   // shift candidates per projection pass
+
 struct Level {
   int n = 0;
   size_t N = 0;
@@ -201,7 +220,9 @@ cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, flo
 
 // ---- launchers (coarse.cu) ----
 cudaError_t launch_level1_assemble(const homo_ctx* c, const Level& L1);
-cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, cudaStream_t s);
+// Galerkin product of level Lf into Lc, one axis at a time; tmp1 (>= 243 n^3 / 2 floats)
+// and tmp2 (>= 243 n^3 / 4) hold the two intermediate stencils (n = Lf.n).
+cudaError_t launch_galerkin(const Level& Lf, const Level& Lc, float* tmp1, float* tmp2, cudaStream_t s);
 cudaError_t launch_coarse_residual(const Level& L, const float* b, const float* x, float* out,
                                    cudaStream_t s);
 cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x, int first,
@@ -239,8 +260,21 @@ cudaError_t launch_cg_update_p(float* p, const float* z, const double* scal, siz
 cudaError_t launch_split_set(float* hi, float* lo, const float* src, size_t n, cudaStream_t s);
 cudaError_t launch_split_get(const float* hi, const float* lo, float* dst, size_t n,
                              cudaStream_t s);
+// Orbit averages of an n^3 element field under the group (in may equal out).
+cudaError_t launch_symmetrize(const SymParam& sp, int n, const float* in, float* out, cudaStream_t s);
+int build_sym_param(int kind, SymParam& sp);
+// y_e = sum over Q_n of w_a Q_a(centre_e) (FP64) into y
+cudaError_t launch_trig_basis(const TrigParam& tp, int n, double* y, cudaStream_t s);
+// per-block sums of S(y - mu_c) for kTrigCand shifts mu_c = mu0 + c * dmu (nv = kTrigCand)
+cudaError_t launch_trig_volume(const double* y, size_t N, double mu0, double dmu, double k, double Vh,
+                               double rho_min, double* part, int* grid_out, cudaStream_t s);
+cudaError_t launch_trig_project(const double* y, size_t N, double mu, double k, double Vh, double rho_min,
+                                float* rho, cudaStream_t s);
 cudaError_t launch_filter(const FilterParam& fp, int n, const float* in, float* out,
                           cudaStream_t s);
+// density-weighted sensitivity filter (out must alias neither rho nor dc)
+cudaError_t launch_sensitivity_filter(const FilterParam& fp, int n, const float* rho, const float* dc,
+                                      float gamma, float* out, cudaStream_t s);
 cudaError_t launch_oc(homo_ctx* c, const float* dc, float* rho, double volfrac, double move,
                       double eta, double rho_min, double* change);
 

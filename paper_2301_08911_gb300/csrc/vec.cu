@@ -301,23 +301,30 @@ __global__ void k_split_get(const float* __restrict__ hi, const float* __restric
 }
 
 // Periodic linear-cone filter: out_e = inv_wsum * sum_k w_k in_(e + off_k).
+// kSens = false: out_e = sum_d w(d) in_(e+d) / sum_d w(d) (density filter, its own
+// adjoint). kSens = true: the density-weighted sensitivity filter of the unfiltered variant
+// (Sec. 5.3), out_e = sum_d w(d) rho_(e+d) in_(e+d) / (max(gamma, rho_e) sum_d w(d)).
+template <bool kSens>
 __global__ void __launch_bounds__(256) k_filter(const __grid_constant__ FilterParam F, int n,
                                                 const float* __restrict__ in,
+                                                const float* __restrict__ rho, float gamma,
                                                 float* __restrict__ out) {
   const size_t N = static_cast<size_t>(n) * n * n;
   for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
        e += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(e % n), y = static_cast<int>((e / n) % n),
-              z = static_cast<int>(e / (static_cast<size_t>(n) * n));
+    int x, y, z;
+    decode3(static_cast<unsigned>(e), static_cast<unsigned>(n), x, y, z);
     float s = 0.f;
     for (int k = 0; k < F.count; ++k) {
       int xx = x + F.off[k][0], yy = y + F.off[k][1], zz = z + F.off[k][2];
       xx += xx < 0 ? n : (xx >= n ? -n : 0);
       yy += yy < 0 ? n : (yy >= n ? -n : 0);
       zz += zz < 0 ? n : (zz >= n ? -n : 0);
-      s = fmaf(F.w[k], __ldg(in + xx + static_cast<size_t>(n) * (yy + static_cast<size_t>(n) * zz)), s);
+      const size_t f = xx + static_cast<size_t>(n) * (yy + static_cast<size_t>(n) * zz);
+      const float v = kSens ? __ldg(in + f) * __ldg(rho + f) : __ldg(in + f);
+      s = fmaf(F.w[k], v, s);
     }
-    out[e] = s * F.inv_wsum;
+    out[e] = kSens ? s * F.inv_wsum / fmaxf(gamma, __ldg(rho + e)) : s * F.inv_wsum;
   }
 }
 
@@ -490,6 +497,97 @@ __global__ void k_max_partials(const double* __restrict__ part, int nblk, double
   *out = m;
 }
 
+// Orbit averages under a cube symmetry group (Sec. 6.1). Thread per element: it forms
+// the indices of the element's images (index arithmetic only) and continues only if its
+// own index is the smallest, i.e. once per orbit; that thread sums the orbit's values in
+// FP64 and writes the average to every member. For values within a factor 2^29 of each
+// other (densities in [1e-3, 1], say) the FP64 sum of at most 48 FP32 values is exact, so
+// the result does not depend on the order and every member gets the same FP32 value.
+// Orbits are disjoint, so the kernel may run in place.
+__device__ __forceinline__ unsigned sym_image(const SymParam& S, int g, int x, int y, int z, int n) {
+  const int c[3] = {x, y, z};
+  int j[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int p = S.perm[g][k];
+    const int v = p == 0 ? c[0] : (p == 1 ? c[1] : c[2]);
+    j[k] = ((S.flip[g] >> k) & 1) ? n - 1 - v : v;
+  }
+  return static_cast<unsigned>(j[0]) + static_cast<unsigned>(n) * (j[1] + static_cast<unsigned>(n) * j[2]);
+}
+
+__global__ void __launch_bounds__(256) k_symmetrize(const __grid_constant__ SymParam S, const float* in,
+                                                    float* out, int n) {
+  const unsigned N = static_cast<unsigned>(n) * n * n;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+    int x, y, z;
+    decode3(e, static_cast<unsigned>(n), x, y, z);
+    bool canonical = true;
+    for (int g = 0; g < S.count && canonical; ++g) canonical = sym_image(S, g, x, y, z, n) >= e;
+    if (!canonical) continue;
+    double acc = 0.0;
+    for (int g = 0; g < S.count; ++g) acc += static_cast<double>(in[sym_image(S, g, x, y, z, n)]);
+    const float avg = static_cast<float>(acc / S.count);
+    for (int g = 0; g < S.count; ++g) out[sym_image(S, g, x, y, z, n)] = avg;
+  }
+}
+
+// Trigonometric initialisation (Sec. 6.2), FP64 throughout (a one-time setup step).
+// Basis order: T index 2 (3 (k - 1) + i) + {0: cos, 1: sin} of 2 pi k xb_i, then the
+// products T_a T_b, a <= b, row by row; xb = R (centre - 1/2).
+__global__ void __launch_bounds__(256) k_trig_basis(const __grid_constant__ TrigParam P, int n, double* y) {
+  const unsigned N = static_cast<unsigned>(n) * n * n;
+  const int nt = 6 * P.nb;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+    int x, yy, z;
+    decode3(e, static_cast<unsigned>(n), x, yy, z);
+    const double c[3] = {(x + 0.5) / n - 0.5, (yy + 0.5) / n - 0.5, (z + 0.5) / n - 0.5};
+    double xb[3];
+    for (int r = 0; r < 3; ++r) xb[r] = P.R[3 * r] * c[0] + P.R[3 * r + 1] * c[1] + P.R[3 * r + 2] * c[2];
+    double T[kTrigMaxT];
+    for (int k = 1; k <= P.nb; ++k)
+      for (int i = 0; i < 3; ++i) {
+        double sv, cv;
+        sincospi(2.0 * k * xb[i], &sv, &cv);
+        T[2 * (3 * (k - 1) + i)] = cv;
+        T[2 * (3 * (k - 1) + i) + 1] = sv;
+      }
+    double acc = 0.0;
+    int idx = 0;
+    for (int a = 0; a < nt; ++a) acc = fma(P.w[idx++], T[a], acc);
+    for (int a = 0; a < nt; ++a)
+      for (int b = a; b < nt; ++b) acc = fma(P.w[idx++], T[a] * T[b], acc);
+    y[e] = acc;
+  }
+}
+
+__device__ __forceinline__ double trig_sigmoid(double y, double mu, double k, double Vh, double rho_min) {
+  const double r = rho_min + Vh / (1.0 + exp(-k * (y - mu)));
+  return fmin(fmax(r, rho_min), 1.0);
+}
+
+__global__ void __launch_bounds__(256) k_trig_volume(const double* __restrict__ y, size_t N, double mu0,
+                                                     double dmu, double k, double Vh, double rho_min,
+                                                     double* __restrict__ part) {
+  double acc[kTrigCand];
+#pragma unroll
+  for (int c = 0; c < kTrigCand; ++c) acc[c] = 0.0;
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    const double v = y[e];
+#pragma unroll
+    for (int c = 0; c < kTrigCand; ++c) acc[c] += trig_sigmoid(v, mu0 + c * dmu, k, Vh, rho_min);
+  }
+  block_sum_store_d<kTrigCand>(acc, part);
+}
+
+__global__ void __launch_bounds__(256) k_trig_project(const double* __restrict__ y, size_t N, double mu,
+                                                      double k, double Vh, double rho_min, float* rho) {
+  for (size_t e = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; e < N;
+       e += static_cast<size_t>(gridDim.x) * blockDim.x)
+    rho[e] = static_cast<float>(trig_sigmoid(y[e], mu, k, Vh, rho_min));
+}
+
 }  // namespace
 
 int reduce_grid(size_t n_items) { return grid_for(n_items, 256); }
@@ -568,10 +666,60 @@ cudaError_t launch_split_get(const float* hi, const float* lo, float* dst, size_
   return cudaGetLastError();
 }
 
+int build_sym_param(int kind, SymParam& sp) {
+  sp.count = 0;
+  const int perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  const int parity[6] = {1, -1, -1, 1, 1, -1};
+  if (kind != HOMO_SYM_REFLECT3 && kind != HOMO_SYM_ROTATE3 && kind != HOMO_SYM_REFLECT6) return HOMO_EINVAL;
+  for (int p = 0; p < 6; ++p)
+    for (int f = 0; f < 8; ++f) {
+      const int det = parity[p] * (((f & 1) + ((f >> 1) & 1) + (f >> 2)) % 2 ? -1 : 1);
+      if (kind == HOMO_SYM_REFLECT3 && p != 0) continue;
+      if (kind == HOMO_SYM_ROTATE3 && det != 1) continue;
+      for (int k = 0; k < 3; ++k) sp.perm[sp.count][k] = static_cast<unsigned char>(perms[p][k]);
+      sp.flip[sp.count] = static_cast<unsigned char>(f);
+      ++sp.count;
+    }
+  return HOMO_OK;
+}
+
+cudaError_t launch_trig_basis(const TrigParam& tp, int n, double* y, cudaStream_t s) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  k_trig_basis<<<grid_for(N, 256), 256, 0, s>>>(tp, n, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trig_volume(const double* y, size_t N, double mu0, double dmu, double k, double Vh,
+                               double rho_min, double* part, int* grid_out, cudaStream_t s) {
+  const int g = grid_for(N, 256);
+  *grid_out = g;
+  k_trig_volume<<<g, 256, 0, s>>>(y, N, mu0, dmu, k, Vh, rho_min, part);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trig_project(const double* y, size_t N, double mu, double k, double Vh, double rho_min,
+                                float* rho, cudaStream_t s) {
+  k_trig_project<<<grid_for(N, 256), 256, 0, s>>>(y, N, mu, k, Vh, rho_min, rho);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(const SymParam& sp, int n, const float* in, float* out, cudaStream_t s) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  k_symmetrize<<<grid_for(N, 256), 256, 0, s>>>(sp, in, out, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_filter(const FilterParam& fp, int n, const float* in, float* out,
                           cudaStream_t s) {
   const size_t N = static_cast<size_t>(n) * n * n;
-  k_filter<<<grid_for(N, 256), 256, 0, s>>>(fp, n, in, out);
+  k_filter<false><<<grid_for(N, 256), 256, 0, s>>>(fp, n, in, nullptr, 0.f, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sensitivity_filter(const FilterParam& fp, int n, const float* rho, const float* dc,
+                                      float gamma, float* out, cudaStream_t s) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  k_filter<true><<<grid_for(N, 256), 256, 0, s>>>(fp, n, dc, rho, gamma, out);
   return cudaGetLastError();
 }
 
