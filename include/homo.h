@@ -80,6 +80,8 @@ typedef struct homo_opts {
   int smoother;     /* HOMO_SMOOTH_GS8 (default) or HOMO_SMOOTH_CHEBYSHEV                */
   int cheb_degree;  /* Chebyshev polynomial degree per sweep, 2..4 (default 2)           */
   int precision;    /* HOMO_PRECISION_FP32 (default) or HOMO_PRECISION_MIXED             */
+  int graphs;       /* 1: replay each CG iteration as a captured CUDA graph (needs a
+                       non-NULL stream; not while profiling), 0 (default): plain launches */
 } homo_opts;
 
 /* Smoothers. GS8: 8-colour block Gauss-Seidel (Sec. 4.1-4.2, Eq. 15-16), colours 0..7
@@ -205,6 +207,22 @@ int homo_set_density(homo_ctx* ctx, const float* rho, int on_device);
  * HOMO_EDIVERGED on a non-finite residual. Synchronises the stream. */
 int homo_solve_cases(homo_ctx* ctx, double rel_tol, int max_iters, int warm_start,
                      int iters_out[6], double relres_out[6]);
+
+/* Solve the cell problems of several contexts (cells of any sizes) together: the contexts
+ * advance their CG iterations in lockstep, each on its own stream, with one host
+ * synchronisation per step for all of them, so small cells overlap on the GPU. Each
+ * context's result is the one homo_solve_cases would give it (same kernels, same order).
+ * With homo_opts.graphs = 1 and a non-NULL stream per context, every CG iteration is one
+ * CUDA graph launch instead of about a hundred kernel launches. (The paper solves one
+ * cell at a time; this entry point has no counterpart there.)
+ *   ctxs: host array of count distinct contexts; rel_tol, max_iters, warm_start as in
+ *   homo_solve_cases. iters_out, relres_out: host arrays of 6 * count (nullable), case
+ *   results of context i at [6 i, 6 i + 6). status_out: host array of count (nullable),
+ *   the status homo_solve_cases would return for context i.
+ * Returns HOMO_EINVAL for bad arguments, otherwise the most severe per-context status
+ * (HOMO_OK < HOMO_ENOCONV < others). */
+int homo_solve_batch(homo_ctx* const* ctxs, int count, double rel_tol, int max_iters, int warm_start,
+                     int* iters_out, double* relres_out, int* status_out);
 
 /* Relative true residual ||f_i - K u_i||_2 / ||f_i||_2 (rigid translations removed) of
  * the context's current displacement fields, per case (0 where f_i = 0), by one of two

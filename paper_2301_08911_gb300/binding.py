@@ -27,7 +27,7 @@ class HomoOpts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int), ("min_coarse", ctypes.c_int),
                 ("max_levels", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("smoother", ctypes.c_int),
-                ("cheb_degree", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("cheb_degree", ctypes.c_int), ("precision", ctypes.c_int), ("graphs", ctypes.c_int)]
 
 
 SMOOTHERS = {"gs8": 0, "chebyshev": 1}
@@ -76,6 +76,8 @@ SIGNATURES = {
     "homo_launch_count": (ctypes.c_longlong, [_vp]),
     "homo_residual_history": (ctypes.c_int, [_vp, _c_double_p, ctypes.c_int]),
     "homo_residual": (ctypes.c_int, [_vp, ctypes.c_int, _c_double_p]),
+    "homo_solve_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_int, _c_int_p, _c_double_p, _c_int_p]),
     "homo_CH_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _c_double_p, _vp]),
 }
 
@@ -125,6 +127,23 @@ def element_matrix(nu: float = 0.3) -> np.ndarray:
     return np.frombuffer(out, dtype=np.float64).reshape(24, 24).copy()
 
 
+def solve_batch(homs, rel_tol: float, max_iters: int = 500, warm_start: bool = True):
+    """Solve the cell problems of several Homogenization contexts together (lockstep CG,
+    one stream per context). Returns (iterations (count, 6), relres (count, 6), statuses)."""
+    lib = load_library()
+    count = len(homs)
+    arr = (_vp * count)(*[h.h for h in homs])
+    its = (ctypes.c_int * (6 * count))()
+    rel = (ctypes.c_double * (6 * count))()
+    st = (ctypes.c_int * count)()
+    rc = lib.homo_solve_batch(arr, count, rel_tol, max_iters, int(warm_start), its, rel, st)
+    if rc not in (HOMO_OK, HOMO_ENOCONV):
+        bad = next((i for i in range(count) if st[i] not in (HOMO_OK, HOMO_ENOCONV)), 0)
+        raise HomoError(rc, lib.homo_last_error(homs[bad].h).decode())
+    return (np.array(its[:], dtype=np.int64).reshape(count, 6), np.array(rel[:]).reshape(count, 6),
+            list(st[:]))
+
+
 def objective(kind: str, CH, iteration: int = 0, param: float = 0.8):
     """f(C^H) and df/dC^H computed by the library (host arithmetic)."""
     lib = load_library()
@@ -142,10 +161,11 @@ class Homogenization:
 
     def __init__(self, n: int, E0: float = 1.0, nu: float = 0.3, p: float = 3.0, Emin: float = 1e-9,
                  min_coarse: int = 0, max_levels: int = 0, sweeps: int = 0, stream=None,
-                 smoother: str = "gs8", cheb_degree: int = 0, precision: str = "fp32"):
+                 smoother: str = "gs8", cheb_degree: int = 0, precision: str = "fp32",
+                 graphs: bool = False):
         self.lib = load_library()
         opts = HomoOpts(ctypes.sizeof(HomoOpts), min_coarse, max_levels, sweeps, sweeps,
-                        SMOOTHERS[smoother], cheb_degree, PRECISIONS[precision])
+                        SMOOTHERS[smoother], cheb_degree, PRECISIONS[precision], int(graphs))
         h = _vp()
         st = self.lib.homo_create(ctypes.byref(h), n, E0, nu, p, Emin, ctypes.byref(opts))
         if st != HOMO_OK:

@@ -63,6 +63,8 @@ void free_all(homo_ctx* c) {
     cudaEventDestroy(r.b);
   }
   for (auto e : c->event_pool) cudaEventDestroy(e);
+  for (auto& g : c->cg_graph)
+    if (g) cudaGraphExecDestroy(g);
 }
 
 bool valid_ptr(const void* p) { return p != nullptr; }
@@ -176,6 +178,12 @@ int ensure_hierarchy(homo_ctx* c) {
       KL(c, HOMO_KC_SETUP, 3, launch_galerkin(c->lev[l], c->lev[l + 1], c->z, c->q, c->stream));
   }
   KL(c, HOMO_KC_SETUP, 3, launch_coarsest_setup(c));
+  if (c->opts.smoother == HOMO_SMOOTH_CHEBYSHEV)   // captured Chebyshev coefficients go stale
+    for (auto& gr : c->cg_graph)
+      if (gr) {
+        cudaGraphExecDestroy(gr);
+        gr = nullptr;
+      }
   for (int l = 1; l + 1 < c->nlev; ++l)
     if (c->lev[l].sth) KL(c, HOMO_KC_SETUP, 1, launch_stencil_bf16(c->lev[l], c->stream));
   if (c->opts.smoother == HOMO_SMOOTH_CHEBYSHEV) RET(estimate_spectra(c));
@@ -326,12 +334,20 @@ int sync_read(homo_ctx* c, int slot, int count) {
   return HOMO_OK;
 }
 
+// Copy count slots from the device to the pinned host mirror (no synchronisation).
+int enq_read(homo_ctx* c, int slot, int count) {
+  CK(c, cudaMemcpyAsync(c->hscal + slot, c->scal + slot, sizeof(double) * count,
+                        cudaMemcpyDeviceToHost, c->stream));
+  return HOMO_OK;
+}
+
 // r = f - K (u + ulo); ||r_c - mean||^2 into S_RR, the plane means (the rigid
-// translations, outside the range of K) into S_RMEAN, active flags, read back.
+// translations, outside the range of K) into S_RMEAN, active flags; enqueues the copy of
+// S_RR to the host (no synchronisation).
 // exact: double-float arithmetic throughout (residuals to ~1e-12 of the terms); otherwise
 // FP32 difference form from both parts of u (accurate to ~1e-7 of sum_d |A_d| |du_d|,
 // several times faster).
-int true_residual(homo_ctx* c, double tol, bool exact) {
+int enq_true_residual(homo_ctx* c, double tol, bool exact) {
   int g = 0;
   if (exact)
     KL(c, HOMO_KC_FINE_RESIDUAL, 1, launch_fine_residual(c, c->f, c->u, c->ulo, c->r, c->part, &g, nullptr));
@@ -340,7 +356,14 @@ int true_residual(homo_ctx* c, double tol, bool exact) {
        launch_fine_tiled(c, 2, c->u, c->f, c->r, c->part, &g, nullptr, 0.f, 0.f, c->ulo));
   KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RR, c->stream));
   KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_active(c->scal, tol, c->N, c->stream));
-  return sync_read(c, S_RR, 6);
+  return enq_read(c, S_RR, 6);
+}
+
+int true_residual(homo_ctx* c, double tol, bool exact) {
+  RET(enq_true_residual(c, tol, exact));
+  CK(c, cudaStreamSynchronize(c->stream));
+  prof_flush(c);
+  return HOMO_OK;
 }
 
 // At tolerances from this one up, a solve starts from the FP32 residual: its error (below
@@ -363,6 +386,303 @@ int precondition_and_direction(homo_ctx* c, int first) {
   KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RZ, c->stream));
   KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_beta(c->scal, first, c->stream));
   KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_update_p(c->pv, c->z, c->scal, c->N, c->stream));
+  return HOMO_OK;
+}
+
+// ---------------------------------------------------------------- CG solve
+// Restarted CG (mixed-precision iterative refinement, u kept in double-float): a cycle runs
+// on the FP32 recursive residual and accumulates its correction in double-float (ecyc +
+// ecyclo), folded into u once per cycle. The residual's plane means (rigid translations,
+// which K cannot produce and the V-cycle would amplify) are tracked and subtracted by every
+// consumer. A cycle ends when every case meets the inner tolerance, has reduced its
+// residual by kCycleDrop, or starts to grow; the next cycle starts from the exact true
+// residual, which also decides convergence.
+//
+// The solve is a state machine: every step enqueues work on the context's stream and asks
+// for one synchronisation before the next step reads the copied residual norms. A single
+// solve is a batch of one; a batch advances many contexts in lockstep, all their streams
+// running concurrently between synchronisations.
+constexpr double kCycleDrop = 1e-5;
+constexpr int kMaxCycles = 24;
+
+struct SolveState {
+  homo_ctx* c = nullptr;
+  double rel_tol = 0.0, inner_tol = 0.0;
+  int max_iters = 0;
+  int its[kCases] = {0, 0, 0, 0, 0, 0};
+  int total = 0, cycle = 0;
+  bool diverged = false, accurate_last = false, first = true;
+  double rr0[kCases] = {}, rrmin[kCases] = {};
+  enum Phase { kInit, kAfterInit, kAfterIter, kAfterCycleRes, kAfterFinalRes, kDone } phase = kInit;
+  int status = HOMO_OK;
+};
+
+bool any_active(SolveState& s, double tol) {
+  homo_ctx* c = s.c;
+  bool a = false;
+  for (int k = 0; k < kCases; ++k) {
+    const double rr = c->hscal[S_RR + k];
+    if (!std::isfinite(rr)) s.diverged = true;
+    if (c->hscal[S_FF + k] > 0.0 && rr > tol * tol * c->hscal[S_FF + k]) a = true;
+  }
+  return a;
+}
+
+bool use_graphs(const homo_ctx* c) { return c->opts.graphs && c->stream && !c->prof; }
+
+void drop_graphs(homo_ctx* c) {
+  for (auto& g : c->cg_graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// One CG iteration: direction from the preconditioned residual, product, step, new residual
+// norms, copy of the norms to the host.
+int enq_iteration(homo_ctx* c, int first, double inner_tol) {
+  int g = 0;
+  RET(precondition_and_direction(c, first));
+  KL(c, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(c, c->pv, c->q, c->part, &g));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_PQ, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_alpha(c->scal, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1,
+     launch_cg_update_er(c->ecyc, c->ecyclo, c->r, c->pv, c->q, c->scal, c->N, c->part, &g, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RR, c->stream));
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_active(c->scal, inner_tol, c->N, c->stream));
+  return enq_read(c, S_RR, 6);
+}
+
+// The same, replayed from a captured graph when the context asks for graphs. Kernel
+// arguments are captured by value: pointers, sizes and the inner tolerance (recaptured
+// when it changes); the smoother's Chebyshev coefficients make the graphs stale whenever
+// the hierarchy is rebuilt (dropped in ensure_hierarchy).
+int run_iteration(homo_ctx* c, int first, double inner_tol) {
+  if (!use_graphs(c)) return enq_iteration(c, first, inner_tol);
+  if (c->cg_graph[first] && c->cg_graph_tol != inner_tol) drop_graphs(c);
+  if (!c->cg_graph[first]) {
+    const long long l0 = c->launches;
+    CK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = enq_iteration(c, first, inner_tol);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    if (rc != HOMO_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_err(c, e, "CG iteration graph capture");
+    const cudaError_t ei = cudaGraphInstantiate(&c->cg_graph[first], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      c->cg_graph[first] = nullptr;
+      return cuda_err(c, ei, "CG iteration graph instantiation");
+    }
+    c->cg_graph_launches[first] = c->launches - l0;
+    c->cg_graph_tol = inner_tol;
+    c->launches = l0;
+  }
+  CK(c, cudaGraphLaunch(c->cg_graph[first], c->stream));
+  c->launches += c->cg_graph_launches[first];
+  return HOMO_OK;
+}
+
+void finish_solve(SolveState& s, int* iters_out, double* relres_out) {
+  homo_ctx* c = s.c;
+  c->solved = true;
+  bool conv = true;
+  for (int k = 0; k < kCases; ++k) {
+    const double ff = c->hscal[S_FF + k], rr = c->hscal[S_RR + k];
+    const double rel = ff > 0.0 ? std::sqrt(rr / ff) : 0.0;
+    if (!std::isfinite(rr)) s.diverged = true;
+    if (ff > 0.0 && !(rel <= s.rel_tol)) conv = false;
+    if (relres_out) relres_out[k] = rel;
+    if (iters_out) iters_out[k] = s.its[k];
+  }
+  if (s.diverged) s.status = set_err(c, HOMO_EDIVERGED, "non-finite residual in CG");
+  else if (!conv) s.status = set_err(c, HOMO_ENOCONV, "relative residual above tolerance after max_iters");
+  s.phase = SolveState::kDone;
+}
+
+// Close the solve: confirm with the exact residual unless the last cycle did.
+// Returns true when work was enqueued (a synchronisation is needed).
+bool begin_finish(SolveState& s, int* iters_out, double* relres_out) {
+  if (!s.accurate_last && !s.diverged) {
+    s.status = enq_true_residual(s.c, s.rel_tol, true);
+    if (s.status != HOMO_OK) {
+      s.phase = SolveState::kDone;
+      return false;
+    }
+    s.phase = SolveState::kAfterFinalRes;
+    return true;
+  }
+  finish_solve(s, iters_out, relres_out);
+  return false;
+}
+
+bool begin_iteration(SolveState& s, int* iters_out, double* relres_out);
+
+// End a cycle: fold the correction into u and recompute the exact residual.
+bool end_cycle(SolveState& s, int* iters_out, double* relres_out) {
+  homo_ctx* c = s.c;
+  int rc = HOMO_OK;
+  {
+    auto k = [&]() -> int {
+      KL(c, HOMO_KC_CG_VECTOR, 1, launch_fold(c->u, c->ulo, c->ecyc, c->ecyclo, kPlanes * c->N, c->stream));
+      return HOMO_OK;
+    };
+    rc = k();
+  }
+  if (rc != HOMO_OK) {
+    s.status = rc;
+    s.phase = SolveState::kDone;
+    return false;
+  }
+  if (s.diverged) return begin_finish(s, iters_out, relres_out);
+  s.status = enq_true_residual(c, s.rel_tol, true);   // recursive and true residual can drift apart
+  if (s.status != HOMO_OK) {
+    s.phase = SolveState::kDone;
+    return false;
+  }
+  s.phase = SolveState::kAfterCycleRes;
+  return true;
+}
+
+// Start a cycle, or finish when nothing is left to do.
+bool begin_cycle(SolveState& s, int* iters_out, double* relres_out) {
+  if (s.cycle >= kMaxCycles || s.diverged || !any_active(s, s.rel_tol) || s.total >= s.max_iters)
+    return begin_finish(s, iters_out, relres_out);
+  for (int k = 0; k < kCases; ++k) s.rr0[k] = s.rrmin[k] = s.c->hscal[S_RR + k];
+  s.first = true;
+  return begin_iteration(s, iters_out, relres_out);
+}
+
+bool begin_iteration(SolveState& s, int* iters_out, double* relres_out) {
+  homo_ctx* c = s.c;
+  if (s.total >= s.max_iters) return end_cycle(s, iters_out, relres_out);
+  ++s.total;
+  for (int k = 0; k < kCases; ++k)
+    if (c->hscal[S_FF + k] > 0.0 && c->hscal[S_RR + k] > s.inner_tol * s.inner_tol * c->hscal[S_FF + k]) ++s.its[k];
+  s.status = run_iteration(c, s.first ? 1 : 0, s.inner_tol);
+  if (s.status != HOMO_OK) {
+    s.phase = SolveState::kDone;
+    return false;
+  }
+  s.first = false;
+  s.phase = SolveState::kAfterIter;
+  return true;
+}
+
+// Advance after the previous step's work has completed. Returns true when new work was
+// enqueued and a synchronisation is needed before the next call.
+bool advance(SolveState& s, int warm_start, int* iters_out, double* relres_out) {
+  homo_ctx* c = s.c;
+  switch (s.phase) {
+    case SolveState::kInit: {
+      s.status = ensure_hierarchy(c);
+      if (s.status != HOMO_OK) break;
+      const size_t V = kPlanes * c->N;
+      auto enq = [&]() -> int {
+        if (!warm_start) {
+          CK(c, cudaMemsetAsync(c->u, 0, sizeof(float) * V, c->stream));
+          CK(c, cudaMemsetAsync(c->ulo, 0, sizeof(float) * V, c->stream));
+        }
+        int g = 0;
+        KL(c, HOMO_KC_CG_VECTOR, 1, launch_dot6(c->f, c->f, c->N, c->part, &g, c->stream));
+        KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases, c->scal + S_FF, c->stream));
+        RET(enq_true_residual(c, s.inner_tol, s.rel_tol < kFastStartTol));
+        RET(enq_read(c, S_FF, 6));
+        // the coarsest factorisation reports a failed pivot in an int next to the OC slots
+        RET(enq_read(c, S_OC + 63, 1));
+        CK(c, cudaMemsetAsync(c->ecyc, 0, sizeof(float) * V, c->stream));
+        CK(c, cudaMemsetAsync(c->ecyclo, 0, sizeof(float) * V, c->stream));
+        return HOMO_OK;
+      };
+      s.status = enq();
+      if (s.status != HOMO_OK) break;
+      s.phase = SolveState::kAfterInit;
+      return true;
+    }
+    case SolveState::kAfterInit: {
+      int piv_fail = 0;
+      std::memcpy(&piv_fail, c->hscal + S_OC + 63, sizeof(int));
+      if (piv_fail) {
+        s.status = set_err(c, HOMO_EDIVERGED, "coarsest operator is not positive definite");
+        break;
+      }
+      c->history.clear();
+      record_history(c);
+      return begin_cycle(s, iters_out, relres_out);
+    }
+    case SolveState::kAfterIter: {
+      record_history(c);
+      if (!any_active(s, s.inner_tol) || s.diverged) return end_cycle(s, iters_out, relres_out);
+      bool cycle_done = true, blowup = false;
+      for (int k = 0; k < kCases; ++k) {
+        const double rr = c->hscal[S_RR + k], ff = c->hscal[S_FF + k];
+        const bool act = ff > 0.0 && rr > s.inner_tol * s.inner_tol * ff;
+        if (act && rr > kCycleDrop * kCycleDrop * s.rr0[k]) cycle_done = false;
+        if (rr > 1e4 * s.rrmin[k]) blowup = true;
+        s.rrmin[k] = std::min(s.rrmin[k], rr);
+      }
+      if (cycle_done || blowup) return end_cycle(s, iters_out, relres_out);
+      return begin_iteration(s, iters_out, relres_out);
+    }
+    case SolveState::kAfterCycleRes:
+      s.accurate_last = true;
+      record_history(c);
+      ++s.cycle;
+      return begin_cycle(s, iters_out, relres_out);
+    case SolveState::kAfterFinalRes:
+      record_history(c);
+      finish_solve(s, iters_out, relres_out);
+      return false;
+    case SolveState::kDone:
+      return false;
+  }
+  s.phase = SolveState::kDone;   // an error ended this solve
+  return false;
+}
+
+// Lockstep driver: every context advances by one step, then every context with pending
+// work is synchronised (their streams ran concurrently), until all are done. Per-context
+// status in status[i]; the return value is HOMO_OK unless an argument is invalid.
+int solve_batch(homo_ctx* const* ctxs, int count, double rel_tol, int max_iters, int warm_start,
+                int* iters_out, double* relres_out, int* status) {
+  if (!(rel_tol > 0.0) || max_iters < 1) {
+    for (int i = 0; i < count; ++i) set_err(ctxs[i], HOMO_EINVAL, "rel_tol > 0 and max_iters >= 1 required");
+    return HOMO_EINVAL;
+  }
+  std::vector<SolveState> st(count);
+  // cycles aim slightly below the tolerance on the recursive residual; with the correction
+  // kept in double-float the exact check that closes a cycle agrees with it to a few
+  // digits, so it normally passes without another cycle
+  for (int i = 0; i < count; ++i) {
+    st[i].c = ctxs[i];
+    st[i].rel_tol = rel_tol;
+    st[i].inner_tol = 0.9 * rel_tol;
+    st[i].max_iters = max_iters;
+  }
+  std::vector<char> pending(count, 0);
+  for (;;) {
+    bool any = false;
+    for (int i = 0; i < count; ++i) {
+      if (st[i].phase == SolveState::kDone) continue;
+      pending[i] = advance(st[i], warm_start, iters_out ? iters_out + kCases * i : nullptr,
+                           relres_out ? relres_out + kCases * i : nullptr) ? 1 : 0;
+      any = any || pending[i];
+    }
+    if (!any) break;
+    for (int i = 0; i < count; ++i) {
+      if (!pending[i]) continue;
+      const cudaError_t e = cudaStreamSynchronize(ctxs[i]->stream);
+      if (e != cudaSuccess) {
+        st[i].status = cuda_err(ctxs[i], e, "solve synchronisation");
+        st[i].phase = SolveState::kDone;
+      }
+      prof_flush(ctxs[i]);
+    }
+  }
+  for (int i = 0; i < count; ++i) status[i] = st[i].status;
   return HOMO_OK;
 }
 
@@ -430,6 +750,7 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
   o.smoother = HOMO_SMOOTH_GS8;
   o.cheb_degree = 2;
   o.precision = HOMO_PRECISION_FP32;
+  o.graphs = 0;
   if (opts) {
     if (opts->struct_size != static_cast<int>(sizeof(homo_opts)))
       return set_err(nullptr, HOMO_EINVAL, "homo_opts.struct_size mismatch");
@@ -440,14 +761,16 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
     o.smoother = opts->smoother;
     if (opts->cheb_degree) o.cheb_degree = opts->cheb_degree;
     o.precision = opts->precision;
+    o.graphs = opts->graphs;
   }
   if (o.min_coarse < 3 || o.max_levels < 0 || o.max_levels > kMaxLevels || o.pre_sweeps < 0 ||
       o.post_sweeps < 0 || o.pre_sweeps > 16 || o.post_sweeps > 16 || o.pre_sweeps != o.post_sweeps ||
       (o.smoother != HOMO_SMOOTH_GS8 && o.smoother != HOMO_SMOOTH_CHEBYSHEV) || o.cheb_degree < 2 ||
-      o.cheb_degree > 4 || (o.precision != HOMO_PRECISION_FP32 && o.precision != HOMO_PRECISION_MIXED))
+      o.cheb_degree > 4 || (o.precision != HOMO_PRECISION_FP32 && o.precision != HOMO_PRECISION_MIXED) ||
+      (o.graphs != 0 && o.graphs != 1))
     return set_err(nullptr, HOMO_EINVAL,
                    "bad homo_opts (min_coarse >= 3, pre == post sweeps <= 16, smoother 0/1, degree 2..4, "
-                   "precision 0/1)");
+                   "precision 0/1, graphs 0/1)");
   int sizes[kMaxLevels];
   int nlev = 1;
   sizes[0] = n;
@@ -508,6 +831,10 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
   if (rc == HOMO_OK) {
     cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&c->hscal), sizeof(double) * S_COUNT);
     if (e != cudaSuccess) rc = cuda_err(c, e, "pinned scalars");
+  }
+  if (rc == HOMO_OK) {
+    cudaError_t e = tiled_init();
+    if (e != cudaSuccess) rc = cuda_err(c, e, "tiled kernel attributes");
   }
   if (rc == HOMO_OK) {
     cudaError_t e = cudaMemset(c->u, 0, sizeof(float) * V);
@@ -648,103 +975,28 @@ int homo_set_density(homo_ctx* ctx, const float* rho, int on_device) {
 int homo_solve_cases(homo_ctx* ctx, double rel_tol, int max_iters, int warm_start,
                      int iters_out[6], double relres_out[6]) {
   if (!ctx) return HOMO_EINVAL;
-  homo_ctx* c = ctx;
-  if (!(rel_tol > 0.0) || max_iters < 1) return set_err(c, HOMO_EINVAL, "rel_tol > 0 and max_iters >= 1 required");
-  RET(ensure_hierarchy(c));
-  const size_t V = kPlanes * c->N;
-  if (!warm_start) {
-    CK(c, cudaMemsetAsync(c->u, 0, sizeof(float) * V, c->stream));
-    CK(c, cudaMemsetAsync(c->ulo, 0, sizeof(float) * V, c->stream));
+  homo_ctx* const list[1] = {ctx};
+  int st = HOMO_OK;
+  const int rc = solve_batch(list, 1, rel_tol, max_iters, warm_start, iters_out, relres_out, &st);
+  return rc == HOMO_OK ? st : rc;
+}
+
+int homo_solve_batch(homo_ctx* const* ctxs, int count, double rel_tol, int max_iters, int warm_start,
+                     int* iters_out, double* relres_out, int* status_out) {
+  if (!ctxs || count < 1) return set_err(nullptr, HOMO_EINVAL, "solve_batch: no contexts");
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i]) return set_err(nullptr, HOMO_EINVAL, "solve_batch: NULL context");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return set_err(nullptr, HOMO_EINVAL, "solve_batch: a context appears twice");
   }
-  int g = 0;
-  KL(c, HOMO_KC_CG_VECTOR, 1, launch_dot6(c->f, c->f, c->N, c->part, &g, c->stream));
-  KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases, c->scal + S_FF, c->stream));
-  // the coarsest factorisation reports a failed pivot in an int next to the OC slots
-  int its[kCases] = {0, 0, 0, 0, 0, 0};
-  int total = 0;
-  bool diverged = false;
-  // cycles aim slightly below the tolerance on the recursive residual; with the correction
-  // kept in double-float the accurate check that closes a cycle agrees with it to a few
-  // digits, so it normally passes without another cycle
-  const double inner_tol = 0.9 * rel_tol;
-  RET(true_residual(c, inner_tol, rel_tol < kFastStartTol));
-  RET(sync_read(c, S_FF, 6));
-  RET(sync_read(c, S_OC + 63, 1));
-  int piv_fail = 0;
-  std::memcpy(&piv_fail, c->hscal + S_OC + 63, sizeof(int));
-  if (piv_fail) return set_err(c, HOMO_EDIVERGED, "coarsest operator is not positive definite");
-  auto any_active = [&](double* rr, double tol) {
-    bool a = false;
-    for (int k = 0; k < kCases; ++k) {
-      if (!std::isfinite(rr[k])) diverged = true;
-      if (c->hscal[S_FF + k] > 0.0 && rr[k] > tol * tol * c->hscal[S_FF + k]) a = true;
-    }
-    return a;
-  };
-  c->history.clear();
-  record_history(c);
-  // Restarted CG (mixed-precision iterative refinement, u kept in double-float): a cycle
-  // runs on the FP32 recursive residual and accumulates its correction in double-float
-  // (ecyc + ecyclo), folded into u once per cycle. The residual's plane means (rigid
-  // translations, which K cannot produce and the V-cycle would amplify) are tracked and
-  // subtracted by every consumer. A cycle ends when every case meets rel_tol, has reduced its residual by
-  // kCycleDrop, or starts to grow; the next cycle starts from the accurate true residual.
-  constexpr double kCycleDrop = 1e-5;
-  double rr0[kCases], rrmin[kCases];
-  CK(c, cudaMemsetAsync(c->ecyc, 0, sizeof(float) * V, c->stream));
-  CK(c, cudaMemsetAsync(c->ecyclo, 0, sizeof(float) * V, c->stream));
-  bool accurate_last = false;
-  for (int restart = 0; restart < 24 && !diverged; ++restart) {
-    if (!any_active(c->hscal + S_RR, rel_tol) || total >= max_iters) break;
-    for (int k = 0; k < kCases; ++k) rr0[k] = rrmin[k] = c->hscal[S_RR + k];
-    RET(precondition_and_direction(c, 1));
-    while (total < max_iters) {
-      ++total;
-      for (int k = 0; k < kCases; ++k)
-        if (c->hscal[S_FF + k] > 0.0 && c->hscal[S_RR + k] > inner_tol * inner_tol * c->hscal[S_FF + k]) ++its[k];
-      KL(c, HOMO_KC_FINE_MATVEC, 1, launch_fine_apply(c, c->pv, c->q, c->part, &g));
-      KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_PQ, c->stream));
-      KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_alpha(c->scal, c->stream));
-      KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_update_er(c->ecyc, c->ecyclo, c->r, c->pv, c->q, c->scal, c->N, c->part, &g, c->stream));
-      KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RR, c->stream));
-      KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_active(c->scal, inner_tol, c->N, c->stream));
-      RET(sync_read(c, S_RR, 6));
-      record_history(c);
-      if (!any_active(c->hscal + S_RR, inner_tol) || diverged) break;
-      bool cycle_done = true, blowup = false;
-      for (int k = 0; k < kCases; ++k) {
-        const double rr = c->hscal[S_RR + k], ff = c->hscal[S_FF + k];
-        const bool act = ff > 0.0 && rr > inner_tol * inner_tol * ff;
-        if (act && rr > kCycleDrop * kCycleDrop * rr0[k]) cycle_done = false;
-        if (rr > 1e4 * rrmin[k]) blowup = true;
-        rrmin[k] = std::min(rrmin[k], rr);
-      }
-      if (cycle_done || blowup) break;
-      RET(precondition_and_direction(c, 0));
-    }
-    KL(c, HOMO_KC_CG_VECTOR, 1, launch_fold(c->u, c->ulo, c->ecyc, c->ecyclo, V, c->stream));
-    if (diverged) break;
-    RET(true_residual(c, rel_tol, true));   // recursive and true residual can drift apart
-    accurate_last = true;
-    record_history(c);
+  std::vector<int> st(count, HOMO_OK);
+  const int rc = solve_batch(ctxs, count, rel_tol, max_iters, warm_start, iters_out, relres_out, st.data());
+  int worst = HOMO_OK;
+  for (int i = 0; i < count; ++i) {
+    if (status_out) status_out[i] = st[i];
+    if (worst == HOMO_OK || (worst == HOMO_ENOCONV && st[i] != HOMO_OK)) worst = st[i];
   }
-  if (!accurate_last && !diverged) {  // converged on the starting residual: confirm
-    RET(true_residual(c, rel_tol, true));
-    record_history(c);
-  }
-  c->solved = true;
-  bool conv = true;
-  for (int k = 0; k < kCases; ++k) {
-    const double ff = c->hscal[S_FF + k], rr = c->hscal[S_RR + k];
-    const double rel = ff > 0.0 ? std::sqrt(rr / ff) : 0.0;
-    if (!std::isfinite(rr)) diverged = true;
-    if (ff > 0.0 && !(rel <= rel_tol)) conv = false;
-    if (relres_out) relres_out[k] = rel;
-    if (iters_out) iters_out[k] = its[k];
-  }
-  if (diverged) return set_err(c, HOMO_EDIVERGED, "non-finite residual in CG");
-  if (!conv) return set_err(c, HOMO_ENOCONV, "relative residual above tolerance after max_iters");
-  return HOMO_OK;
+  return rc == HOMO_OK ? worst : rc;
 }
 
 int homo_residual(homo_ctx* ctx, int method, double relres_out[6]) {

@@ -106,6 +106,40 @@ void build_level1_tables(const KeParam& ke, float* Bf) {
   }
 }
 
+// Eigen-decomposition of a symmetric n x n matrix (n <= 8) by cyclic Jacobi rotations in
+// double: on return a is diagonal (the eigenvalues) and column k of v is eigenvector k.
+void sym_eigen(int n, double* a, double* v) {
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) v[r * n + c] = r == c ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += a[p * n + q] * a[p * n + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        if (std::fabs(a[p * n + q]) < 1e-300) continue;
+        const double th = 0.5 * std::atan2(2 * a[p * n + q], a[q * n + q] - a[p * n + p]);
+        const double cs = std::cos(th), sn = std::sin(th);
+        for (int k = 0; k < n; ++k) {   // rotate columns p, q
+          const double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = cs * akp - sn * akq;
+          a[k * n + q] = sn * akp + cs * akq;
+        }
+        for (int k = 0; k < n; ++k) {   // rotate rows p, q
+          const double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = cs * apk - sn * aqk;
+          a[q * n + k] = sn * apk + cs * aqk;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double vkp = v[k * n + p], vkq = v[k * n + q];
+          v[k * n + p] = cs * vkp - sn * vkq;
+          v[k * n + q] = sn * vkp + cs * vkq;
+        }
+      }
+  }
+}
+
 // Largest eigenvalue of D_e^-1 K0, D_e the 3x3 block diagonal of K0. With
 // x^T K x = sum_e E_e x_e^T K0 x_e <= lam sum_e E_e x_e^T D_e x_e = lam x^T D x it bounds
 // the spectrum of D^-1 K on the finest level for any moduli E. Power iteration on the

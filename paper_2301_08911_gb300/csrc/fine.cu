@@ -195,8 +195,9 @@ __global__ void k_simp(const float* __restrict__ rin, float* __restrict__ rout,
 }
 
 struct ElemParam {
-  float gsym[21];   // objective gradient folded onto the 21 (i <= j) pairs
-  float p, dE;      // SIMP exponent, E0 - Emin
+  float mu[kCases];           // eigenvalues of the symmetrised objective gradient G
+  float vec[kCases][kCases];  // vec[k][i]: component i of the eigenvector of mu[k]
+  float p, dE;                // SIMP exponent, E0 - Emin
   float invN;
 };
 
@@ -218,7 +219,11 @@ __host__ __device__ constexpr int pair_slot(int i, int j) {
 // pairs dealt to it (q_ij = q_ji: the diagonal, i+1, i+2 and, for i < 3, i+3 mod 6, so
 // 3 or 4 each), reading the other w_j from shared memory.
 // MODE 0: block partial sums of E_e q_ij (21 values, Kahan-compensated per thread).
-// MODE 1: sensitivity (Eq. 8-9) p rho^(p-1) dE sum_ij g_ij q_ij / N.
+// MODE 1: sensitivity (Eq. 8-9) p rho^(p-1) dE sum_ij g_ij q_ij / N, evaluated as
+// sum_k mu_k z_k^T K0 z_k with G = sym(g) = sum_k mu_k v_k v_k^T and z_k = sum_i v_k[i] w_i
+// (thread k forms z_k from the six w_i in shared memory): each term is a non-negative
+// quadratic form, so the sum does not cancel across the 21 products (for the bulk
+// objective G has rank one and the sensitivity is a single quadratic form).
 template <int MODE>
 __global__ void __launch_bounds__(kElemBlock) k_fine_elem(const __grid_constant__ KeParam K,
                                                           const __grid_constant__ ChiParam X,
@@ -271,6 +276,15 @@ __global__ void __launch_bounds__(kElemBlock) k_fine_elem(const __grid_constant_
 #pragma unroll
     for (int r = 0; r < 24; ++r) ws[i][lane][r] = w[r];
     __syncthreads();
+    if (MODE == 1) {   // z_k = sum_i v_k[i] w_i replaces w: thread i now stands for mode k = i
+#pragma unroll
+      for (int r = 0; r < 24; ++r) {
+        float zr = 0.f;
+#pragma unroll
+        for (int c = 0; c < kCases; ++c) zr = fmaf(P.vec[i][c], ws[c][lane][r], zr);
+        w[r] = zr;
+      }
+    }
     float yv[24];
 #pragma unroll
     for (int r = 0; r < 24; ++r) yv[r] = 0.f;
@@ -279,16 +293,23 @@ __global__ void __launch_bounds__(kElemBlock) k_fine_elem(const __grid_constant_
 #pragma unroll
       for (int r = 0; r < 24; ++r) yv[r] = fmaf(K.k[r * 24 + k], w[k], yv[r]);
     }
-    float q[4];
+    float q[4] = {0.f, 0.f, 0.f, 0.f};
+    if (MODE == 1) {
+      float t = 0.f;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      float sdot = 0.f;
-      if (k < npair) {
-        const float* wj = ws[jp[k]][lane];
+      for (int r = 0; r < 24; ++r) t = fmaf(yv[r], w[r], t);
+      q[0] = P.mu[i] * t;
+    } else {
 #pragma unroll
-        for (int r = 0; r < 24; ++r) sdot = fmaf(yv[r], wj[r], sdot);
+      for (int k = 0; k < 4; ++k) {
+        float sdot = 0.f;
+        if (k < npair) {
+          const float* wj = ws[jp[k]][lane];
+#pragma unroll
+          for (int r = 0; r < 24; ++r) sdot = fmaf(yv[r], wj[r], sdot);
+        }
+        q[k] = sdot;
       }
-      q[k] = sdot;
     }
     if (MODE == 0) {
       if (live) {
@@ -302,10 +323,7 @@ __global__ void __launch_bounds__(kElemBlock) k_fine_elem(const __grid_constant_
         }
       }
     } else {
-      float sg = 0.f;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) sg = fmaf(k < npair ? P.gsym[slot[k]] : 0.f, q[k], sg);
-      sp[i][lane] = sg;
+      sp[i][lane] = q[0];
     }
     __syncthreads();
     if (MODE == 1 && i == 0 && live) {
@@ -375,11 +393,15 @@ cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float*
 cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, float* sens,
                              double* part, int* grid_out) {
   ElemParam P{};
-  if (g36) {
-    int idx = 0;
+  if (g36) {   // sum_ij g_ij q_ij = sum_ij G_ij q_ij, G = (g + g^T) / 2 = sum_k mu_k v_k v_k^T
+    double G[kCases * kCases], V[kCases * kCases];
     for (int i = 0; i < kCases; ++i)
-      for (int j = i; j < kCases; ++j)
-        P.gsym[idx++] = static_cast<float>(i == j ? g36[6 * i + j] : g36[6 * i + j] + g36[6 * j + i]);
+      for (int j = 0; j < kCases; ++j) G[i * kCases + j] = 0.5 * (g36[6 * i + j] + g36[6 * j + i]);
+    sym_eigen(kCases, G, V);
+    for (int k = 0; k < kCases; ++k) {
+      P.mu[k] = static_cast<float>(G[k * kCases + k]);
+      for (int i = 0; i < kCases; ++i) P.vec[k][i] = static_cast<float>(V[i * kCases + k]);
+    }
   }
   P.p = static_cast<float>(c->p);
   P.dE = static_cast<float>(c->E0 - c->Emin);

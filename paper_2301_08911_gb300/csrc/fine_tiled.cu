@@ -5,7 +5,7 @@
 // current plane is computed, so global latency overlaps the arithmetic. Each thread
 // builds the 27 coupling blocks A_d of its vertex (Eq. 13) from the moduli and the
 // element matrix in the parameter bank and applies them to the 6 load cases.
-#include "dev_common.cuh"
+#include "stencil.cuh"
 
 namespace homo {
 
@@ -33,44 +33,7 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-__device__ __forceinline__ void tile_block(const KeParam& K, const float (&Et)[8], int dx, int dy,
-                                           int dz, float (&A)[9]) {
-#pragma unroll
-  for (int q = 0; q < 9; ++q) A[q] = 0.f;
-#pragma unroll
-  for (int t = 0; t < 8; ++t) {
-    const int ja = dx + 1 - (t & 1), jb = dy + 1 - ((t >> 1) & 1), jc = dz + 1 - (t >> 2);
-    if (ja < 0 || ja > 1 || jb < 0 || jb > 1 || jc < 0 || jc > 1) continue;
-    const int j = ja + 2 * jb + 4 * jc, row = 7 - t;
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        A[3 * r + c] = fmaf(Et[t], K.k[(3 * row + r) * 24 + 3 * j + c], A[3 * r + c]);
-  }
-}
 
-// Solve the SPD 3x3 system S y = b for the 6 cases in place (LDL^T, FP32).
-__device__ __forceinline__ void solve3x6t(const float (&S)[9], float (&b)[18]) {
-  const float d0 = S[0];
-  const float l10 = S[3] / d0, l20 = S[6] / d0;
-  const float d1 = S[4] - l10 * S[1];
-  const float l21 = (S[7] - l20 * S[1]) / d1;
-  const float d2 = S[8] - l20 * S[2] - l21 * (S[5] - l10 * S[2]);
-  const float i0 = 1.f / d0, i1 = 1.f / d1, i2 = 1.f / d2;
-#pragma unroll
-  for (int c = 0; c < kCases; ++c) {
-    float y0 = b[3 * c], y1 = b[3 * c + 1], y2 = b[3 * c + 2];
-    y1 -= l10 * y0;
-    y2 -= l20 * y0 + l21 * y1;
-    const float x2 = y2 * i2;
-    const float x1 = y1 * i1 - l21 * x2;
-    const float x0 = y0 * i0 - l10 * x1 - l20 * x2;
-    b[3 * c] = x0;
-    b[3 * c + 1] = x1;
-    b[3 * c + 2] = x2;
-  }
-}
 
 // Per-thread load sites (fixed for every plane): halo site tid and, if it exists,
 // tid + 256, as in-plane offsets gy*n + gx; same for the moduli tile.
@@ -218,7 +181,7 @@ __global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
         if (kDiff && d == 13) continue;
         const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
         float A[9];
-        tile_block(K, Et, dx, dy, dz, A);
+        nb_block(K, Et, dx, dy, dz, A);
         if (kCheb && d == 13) {
 #pragma unroll
           for (int q = 0; q < 9; ++q) S[q] = A[q];
@@ -244,7 +207,7 @@ __global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
 #pragma unroll
         for (int q = 0; q < kPlanes; ++q)
           acc[q] = (__ldg(b + q * N + v) - (bmean ? static_cast<float>(bmean[q]) : 0.f)) - acc[q];
-        solve3x6t(S, acc);
+        solve3x6(S, acc);
 #pragma unroll
         for (int q = 0; q < kPlanes; ++q) {
           const size_t o = q * N + v;
@@ -299,15 +262,28 @@ namespace {
 template <int MODE>
 cudaError_t run_tiled(const homo_ctx* c, dim3 grid, int zc, const float* u, const float* ulo, const float* b,
                       float* out, double* part, const double* bmean, float c0, float c1) {
-  const size_t shm = tiled_smem_bytes(MODE);
-  cudaError_t e = cudaFuncSetAttribute(k_fine_tiled<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       static_cast<int>(shm));
-  if (e != cudaSuccess) return e;
+  const size_t shm = tiled_smem_bytes(MODE);   // limit set by tiled_init at context creation
   k_fine_tiled<MODE><<<grid, kTiledThreads, shm, c->stream>>>(c->ke, c->E, u, ulo, b, out, c->n, zc, part,
                                                               bmean, c0, c1);
   return cudaGetLastError();
 }
 }  // namespace
+
+template <int MODE>
+cudaError_t tiled_attr() {
+  return cudaFuncSetAttribute(k_fine_tiled<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(tiled_smem_bytes(MODE)));
+}
+
+cudaError_t tiled_init() {
+  cudaError_t e = tiled_attr<1>();
+  if (e == cudaSuccess) e = tiled_attr<2>();
+  if (e == cudaSuccess) e = tiled_attr<3>();
+  if (e == cudaSuccess) e = tiled_attr<4>();
+  if (e == cudaSuccess) e = tiled_attr<5>();
+  if (e == cudaSuccess) e = tiled_attr<6>();
+  return e;
+}
 
 cudaError_t launch_fine_tiled(const homo_ctx* c, int mode, const float* u, const float* b, float* out,
                               double* part, int* grid_out, const double* bmean, float c0, float c1,

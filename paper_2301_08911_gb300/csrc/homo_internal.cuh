@@ -164,6 +164,12 @@ struct homo_ctx {
 
   // Chebyshev smoother: upper end of the spectrum of D^-1 K per smoothed level
   double lam[homo::kMaxLevels] = {};
+
+  // CUDA graphs of one CG iteration (index: first iteration of a cycle or not), captured
+  // on first use after the hierarchy is built and dropped when it is rebuilt
+  cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};
+  long long cg_graph_launches[2] = {0, 0};   // kernels per replay
+  double cg_graph_tol = 0.0;                  // inner tolerance captured in the graphs
 };
 
 namespace homo {
@@ -203,7 +209,11 @@ cudaError_t launch_stencil_bf16(const Level& L, cudaStream_t s);
 cudaError_t launch_fill_hash(float* x, size_t count, unsigned seed, cudaStream_t s);
 // largest eigenvalue of blockdiag(K0)^-1 K0 (host arithmetic)
 double element_jacobi_bound(const KeParam& ke);
+// symmetric n x n eigen-decomposition (n <= 8), double: a -> diag, columns of v eigenvectors
+void sym_eigen(int n, double* a, double* v);
 size_t tiled_smem_bytes(int mode);
+// dynamic shared-memory limit of every tiled mode on the current device (before any capture)
+cudaError_t tiled_init();
 int tiled_grid_blocks(int n);
 // ulo != null: out = b - K (u + ulo) in double-float (accurate true residual) with
 // partials of ||out_c||^2 and plane sums; ulo == null: out = (b - bmean) - K u (bmean: 18

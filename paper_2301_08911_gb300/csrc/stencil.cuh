@@ -14,23 +14,40 @@ __device__ __forceinline__ void load_E8(const float* __restrict__ E, const Nb& n
   for (int t = 0; t < 8; ++t) Et[t] = __ldg(E + nb.X[t & 1] + nb.Y[(t >> 1) & 1] + nb.Z[t >> 2]);
 }
 
-// 3x3 block A_d for neighbour offset (dx,dy,dz); all index arithmetic folds at compile
-// time once the callers' loops are unrolled.
+// 3x3 block A_d for neighbour offset (dx,dy,dz). Reflecting the cube through its centre
+// planes maps any local vertex i to vertex 0 and negates the reflected displacement
+// components, so K0[i][j] = R_i K0[0][i ^ j] R_i with R_i = diag(+-1) (-1 where bit k of
+// i is set). In A_d every contributing element t has i ^ j = |d| (componentwise), hence
+//   A_d[r][c] = K0[0][|d|][r][c] * sum_(t contributing) E_t s_r(t) s_c(t)   (s_r s_c = 1 if r = c),
+// with s_k = d_k on axes where d_k != 0 and s_k = +1 / -1 for elements on the + / - side
+// of v along axes where d_k = 0. So each block is 9 products with signed sums of the 8
+// moduli instead of 9 FMAs per contributing element. All index and sign arithmetic folds
+// at compile time once the callers' loops over d are unrolled.
 __device__ __forceinline__ void nb_block(const KeParam& K, const float (&Et)[8], int dx, int dy,
                                          int dz, float (&A)[9]) {
-#pragma unroll
-  for (int q = 0; q < 9; ++q) A[q] = 0.f;
+  const int D[3] = {dx, dy, dz};
+  const int m = (dx != 0 ? 1 : 0) + (dy != 0 ? 2 : 0) + (dz != 0 ? 4 : 0);
+  float s0 = 0.f, s01 = 0.f, s02 = 0.f, s12 = 0.f;
 #pragma unroll
   for (int t = 0; t < 8; ++t) {
-    const int ja = dx + 1 - (t & 1), jb = dy + 1 - ((t >> 1) & 1), jc = dz + 1 - (t >> 2);
-    if (ja < 0 || ja > 1 || jb < 0 || jb > 1 || jc < 0 || jc > 1) continue;
-    const int j = ja + 2 * jb + 4 * jc, row = 7 - t;
+    const int tb[3] = {t & 1, (t >> 1) & 1, t >> 2};
+    bool in = true;
+    int sg[3];
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        A[3 * r + c] = fmaf(Et[t], K.k[(3 * row + r) * 24 + 3 * j + c], A[3 * r + c]);
+    for (int k = 0; k < 3; ++k) {
+      if ((D[k] == 1 && tb[k] != 1) || (D[k] == -1 && tb[k] != 0)) in = false;
+      sg[k] = D[k] != 0 ? D[k] : (tb[k] ? 1 : -1);
+    }
+    if (!in) continue;
+    s0 += Et[t];
+    s01 += sg[0] * sg[1] > 0 ? Et[t] : -Et[t];
+    s02 += sg[0] * sg[2] > 0 ? Et[t] : -Et[t];
+    s12 += sg[1] * sg[2] > 0 ? Et[t] : -Et[t];
   }
+  const float* C = K.k + 3 * m;   // row r of K0[0][m] starts at K.k[r * 24 + 3 m]
+  A[0] = C[0] * s0;       A[1] = C[1] * s01;      A[2] = C[2] * s02;
+  A[3] = C[24] * s01;     A[4] = C[25] * s0;      A[5] = C[26] * s12;
+  A[6] = C[48] * s02;     A[7] = C[49] * s12;     A[8] = C[50] * s0;
 }
 
 // Solve the SPD 3x3 system S y = b for NC right-hand sides (LDL^T, FP32).
