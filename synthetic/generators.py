@@ -122,27 +122,22 @@ def laminate_density(n: int, axis: int, values) -> np.ndarray:
 
 
 def cubic_symmetric_density(n: int, seed: int, lo: float = 0.2, hi: float = 1.0) -> np.ndarray:
-    """Random field averaged over the 48 symmetries of the cube about the cell centre.
+    """Random field invariant under the 48 symmetries of the cube about the cell centre.
 
-    Voxel centres map to voxel centres under every axis flip and axis permutation, so
-    the result is exactly invariant under the full cubic group.
+    Every voxel draws its value from the sorted absolute offsets of its centre from the
+    cell centre (in half-voxels), a key that every axis flip and axis permutation leaves
+    unchanged; so the field is exactly invariant by construction (no averaging).
     """
-    g = uniform_density(n, seed, lo, hi, np.float64).reshape(n, n, n)
-    acc = np.zeros_like(g)
-    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
-        t = np.transpose(g, perm)
-        for fx in (False, True):
-            for fy in (False, True):
-                for fz in (False, True):
-                    s = t
-                    if fx:
-                        s = s[:, :, ::-1]
-                    if fy:
-                        s = s[:, ::-1, :]
-                    if fz:
-                        s = s[::-1, :, :]
-                    acc += s
-    return (acc / 48.0).reshape(-1).astype(np.float32)
+    c = np.abs(2 * np.arange(n) - (n - 1))               # |2 i - (n - 1)|, per axis
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    a = np.sort(np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1), axis=1)
+    m = n + 1
+    key = (a[:, 0] + m * (a[:, 1] + m * a[:, 2])).astype(np.uint64)
+    with np.errstate(over="ignore"):
+        base = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) * _GOLDEN
+        z = _splitmix64(base + (key + np.uint64(1)) * _GOLDEN)
+    u = (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+    return (lo + (hi - lo) * u).astype(np.float32)
 
 
 def batched_cell_specs(count: int, seed: int, sizes=(32, 48, 64, 96, 128),
