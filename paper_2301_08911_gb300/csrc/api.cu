@@ -52,7 +52,7 @@ void free_all(homo_ctx* c) {
   auto f = [](void* p) {
     if (p) cudaFree(p);
   };
-  f(c->rho); f(c->E); f(c->u); f(c->ulo); f(c->f); f(c->r); f(c->z); f(c->pv); f(c->q);
+  f(c->rho); f(c->E); f(c->u); f(c->ulo); f(c->f); f(c->flo); f(c->r); f(c->z); f(c->pv); f(c->q);
   f(c->tmp); f(c->A); f(c->G); f(c->part); f(c->scal); f(c->ecyc); f(c->ecyclo);
   for (int l = 0; l < kMaxLevels; ++l) {
     f(c->lev[l].st); f(c->lev[l].x); f(c->lev[l].b); f(c->lev[l].t); f(c->lev[l].sth);
@@ -805,7 +805,8 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
     if (rc == HOMO_OK) rc = dalloc(c, ptr, cnt, w);
   };
   A(&c->rho, N, "rho"); A(&c->E, N, "E"); A(&c->tmp, N, "tmp");
-  A(&c->u, V, "u"); A(&c->ulo, V, "ulo"); A(&c->f, V, "f"); A(&c->r, V, "r");
+  A(&c->u, V, "u"); A(&c->ulo, V, "ulo"); A(&c->f, V, "f"); A(&c->flo, V, "f (low part)");
+  A(&c->r, V, "r");
   A(&c->z, V, "z"); A(&c->pv, V, "p"); A(&c->q, V, "q"); A(&c->ecyc, V, "cycle correction");
   A(&c->ecyclo, V, "cycle correction (low)");
   for (int l = 0; l < nlev; ++l) {

@@ -68,6 +68,7 @@ void build_element_matrix(double nu, KeParam& ke, LoadParam& ld, ChiParam& chi) 
       double s = 0;
       for (int c = 0; c < 24; ++c) s += K[r][c] * X[i][c];
       ld.fe[i][r] = static_cast<float>(s);
+      ld.fe_lo[i][r] = static_cast<float>(s - static_cast<double>(ld.fe[i][r]));
       chi.chi[i][r] = static_cast<float>(X[i][r]);
     }
 }

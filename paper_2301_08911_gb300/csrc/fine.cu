@@ -17,36 +17,6 @@ namespace homo {
 
 namespace {
 
-// Macro-strain loads in vertex form (Eq. 11): f_(i,v) = sum_t E_t (K0 chi_i)[7 - t].
-// In a uniform medium the 8 element forces at a vertex cancel exactly (sum_t (K0
-// chi_i)[7 - t] = 0), so the kernel sums (E_t - E_0) (K0 chi_i)[7 - t]: the loads are
-// exactly zero where E is locally uniform and carry no cancellation error elsewhere.
-__global__ void __launch_bounds__(256) k_loads(const __grid_constant__ LoadParam L,
-                                               const float* __restrict__ E,
-                                               float* __restrict__ f, int n) {
-  const size_t N = static_cast<size_t>(n) * n * n;
-  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
-       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
-    const int x = static_cast<int>(v % n), y = static_cast<int>((v / n) % n),
-              z = static_cast<int>(v / (static_cast<size_t>(n) * n));
-    const Nb nb = make_nb(x, y, z, n);
-    float Et[8];
-    load_E8(E, nb, Et);
-    float dE[8];
-#pragma unroll
-    for (int t = 0; t < 8; ++t) dE[t] = Et[t] - Et[0];
-#pragma unroll
-    for (int c = 0; c < kCases; ++c)
-#pragma unroll
-      for (int r = 0; r < 3; ++r) {
-        float s = 0.f;
-#pragma unroll
-        for (int t = 1; t < 8; ++t) s = fmaf(dE[t], L.fe[c][3 * (7 - t) + r], s);
-        f[static_cast<size_t>(3 * c + r) * N + v] = s;
-      }
-  }
-}
-
 // Error-free transformations (Knuth TwoSum, FMA-based TwoProduct) with operations the
 // compiler may not contract or reorder.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -55,7 +25,53 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
 }
 
-// r = b - K (u + ulo) evaluated in double-float arithmetic (difference form, products
+// Macro-strain loads in vertex form (Eq. 11): f_(i,v) = sum_t E_t (K0 chi_i)[7 - t].
+// In a uniform medium the 8 element forces at a vertex cancel exactly (sum_t (K0
+// chi_i)[7 - t] = 0), so the kernel sums (E_t - E_0) (K0 chi_i)[7 - t]: the loads are
+// exactly zero where E is locally uniform and carry no cancellation error elsewhere.
+// The sum is formed in double-float arithmetic (the difference E_t - E_0 and K0 chi split
+// exactly, error-free products and sums) and stored as f + flo: an FP32 load rounded
+// against the largest of its terms perturbs the weakly held soft-region displacements,
+// whose strain energies the sensitivities of Eq. 9 weigh.
+__global__ void __launch_bounds__(256) k_loads(const __grid_constant__ LoadParam L,
+                                               const float* __restrict__ E,
+                                               float* __restrict__ f, float* __restrict__ flo, int n) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  for (size_t v = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; v < N;
+       v += static_cast<size_t>(gridDim.x) * blockDim.x) {
+    int x, y, z;
+    decode3(static_cast<unsigned>(v), static_cast<unsigned>(n), x, y, z);
+    const Nb nb = make_nb(x, y, z, n);
+    float Et[8];
+    load_E8(E, nb, Et);
+    float dh[8], dl[8];
+#pragma unroll
+    for (int t = 1; t < 8; ++t) two_sum(Et[t], -Et[0], dh[t], dl[t]);   // E_t - E_0 = dh + dl
+#pragma unroll
+    for (int c = 0; c < kCases; ++c)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll
+        for (int t = 1; t < 8; ++t) {
+          const float a = L.fe[c][3 * (7 - t) + r], al = L.fe_lo[c][3 * (7 - t) + r];
+          const float p = __fmul_rn(dh[t], a);
+          const float pe = fmaf(dh[t], a, -p);               // dh a = p + pe exactly
+          float s, e;
+          two_sum(hi, p, s, e);
+          hi = s;
+          lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(e, pe), fmaf(dh[t], al, __fmul_rn(dl[t], a))));
+        }
+        const float s2 = __fadd_rn(hi, lo);
+        const size_t o = static_cast<size_t>(3 * c + r) * N + v;
+        f[o] = s2;
+        flo[o] = __fadd_rn(lo, -__fadd_rn(s2, -hi));          // FastTwoSum: f + flo = hi + lo
+      }
+  }
+}
+
+
+// r = (b + blo) - K (u + ulo) evaluated in double-float arithmetic (difference form, products
 // and sums error-free up to the final rounding), then partials of ||r_c||^2 and of the
 // 18 plane sums. This is the accurate true residual the CG driver restarts from; it uses
 // exactly the FP32 blocks A_d of the CG product, so both see the same operator.
@@ -64,6 +80,7 @@ __global__ void __launch_bounds__(128) k_fine_true_residual(const __grid_constan
                                                             const float* __restrict__ u,
                                                             const float* __restrict__ ulo,
                                                             const float* __restrict__ b,
+                                                            const float* __restrict__ blo,
                                                             float* __restrict__ out, int n,
                                                             double* __restrict__ part) {
   const size_t N = static_cast<size_t>(n) * n * n;
@@ -123,7 +140,7 @@ __global__ void __launch_bounds__(128) k_fine_true_residual(const __grid_constan
       const size_t o = static_cast<size_t>(q) * N + v;
       float s, e;
       two_sum(__ldg(b + o), -hi[q], s, e);
-      const float val = __fadd_rn(s, __fadd_rn(e, -lo[q]));
+      const float val = __fadd_rn(s, __fadd_rn(e, __fadd_rn(__ldg(blo + o), -lo[q])));
       out[o] = val;
       red[q / 3] = fmaf(val, val, red[q / 3]);
       red[kCases + q] += val;
@@ -368,7 +385,7 @@ cudaError_t launch_fine_stencil(const homo_ctx* c, const Level& L0) {
 }
 
 cudaError_t launch_loads(const homo_ctx* c, float* f) {
-  k_loads<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->ld, c->E, f, c->n);
+  k_loads<<<grid_for(c->N, 256), 256, 0, c->stream>>>(c->ld, c->E, f, c->flo, c->n);
   return cudaGetLastError();
 }
 
@@ -383,7 +400,7 @@ cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float*
   if (ulo) {
     const int g = grid_for(c->N, 128);
     if (grid_out) *grid_out = g;
-    k_fine_true_residual<<<g, 128, 0, c->stream>>>(c->ke, c->E, u, ulo, b, out, c->n, part);
+    k_fine_true_residual<<<g, 128, 0, c->stream>>>(c->ke, c->E, u, ulo, b, c->flo, out, c->n, part);
     return cudaGetLastError();
   }
   return launch_fine_tiled(c, 3, u, b, out, nullptr, grid_out, bmean);

@@ -38,7 +38,8 @@ struct KeParam {
 // Per-case nodal force of a unit-modulus element under the unit macro strain:
 // fe[i][3j+comp] = (K0 chi_i)[3j+comp] (Eq. 4 with the element-relative chi of Eq. 12).
 struct LoadParam {
-  float fe[kCases][24];
+  float fe[kCases][24];      // K0 chi_i per local dof, high part
+  float fe_lo[kCases][24];   // low part (fe + fe_lo = K0 chi_i to double precision)
 };
 
 // Element-relative unit-strain displacements chi_i (Eq. 12), voxel units.
@@ -125,7 +126,8 @@ struct homo_ctx {
   float* ulo = nullptr;      // displacement low part (u = u + ulo exactly), 18N
   float* ecyc = nullptr;     // correction accumulated during one CG cycle, 18N (high part)
   float* ecyclo = nullptr;   // its low part: the correction is kept in double-float
-  float* f = nullptr;        // loads, 18N
+  float* f = nullptr;        // loads, 18N (high part)
+  float* flo = nullptr;      // low part of the double-float loads, 18N
   float* r = nullptr;        // CG residual, 18N
   float* z = nullptr;        // preconditioned residual, 18N
   float* pv = nullptr;       // CG direction, 18N
@@ -215,7 +217,7 @@ size_t tiled_smem_bytes(int mode);
 // dynamic shared-memory limit of every tiled mode on the current device (before any capture)
 cudaError_t tiled_init();
 int tiled_grid_blocks(int n);
-// ulo != null: out = b - K (u + ulo) in double-float (accurate true residual) with
+// ulo != null: out = (b + flo) - K (u + ulo) in double-float (b must be the loads f; accurate true residual) with
 // partials of ||out_c||^2 and plane sums; ulo == null: out = (b - bmean) - K u (bmean: 18
 // plane means or null).
 cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float* u,

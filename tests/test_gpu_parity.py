@@ -180,8 +180,10 @@ def _solved(B, n, kind, smoother="gs8", precision="fp32"):
     hom = make(B, n, smoother=smoother, precision=precision)
     hom.set_density(cuda(rho_t))
     # well below the configs' 1e-6 so that the comparison measures the kernels' FP32
-    # arithmetic, not the stopping tolerance (the sensitivity error is first order in it)
-    its, relres, _ = hom.solve_cases(1e-9, 600, warm_start=False)
+    # arithmetic, not the stopping tolerance: per-element sensitivities are first order in
+    # the solution error, which at 1e-9 still reaches ~1e-6 through the weakly determined
+    # void modes (moduli 1e-9) of the blurred-noise cell
+    its, relres, _ = hom.solve_cases(1e-10, 800, warm_start=False)
     _CASES[key] = (hom, rho_t, ref, its, relres)
     return _CASES[key]
 
