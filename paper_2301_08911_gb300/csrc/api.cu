@@ -122,10 +122,31 @@ struct Prof {
     CK(ctx, call);                 \
   } while (0)
 
+// Loads of a case whose norm is below this fraction of the largest case's are the
+// rounding residue of a load that is zero in exact arithmetic (in-plane shear of a
+// laminate, say: the double-float loads keep the 1e-16 asymmetries of K0 chi) and are set
+// to zero, so the case is converged at u = 0 instead of chasing a relative tolerance on
+// noise.
+constexpr double kLoadResidue = 1e-12;
+
 int ensure_loads(homo_ctx* c) {
   if (!c->density_set) return set_err(c, HOMO_ESTATE, "no density set (call homo_set_density first)");
   if (!c->loads_valid) {
     KL(c, HOMO_KC_SETUP, 1, launch_loads(c, c->f));
+    int g = 0;
+    KL(c, HOMO_KC_SETUP, 1, launch_dot6(c->f, c->f, c->N, c->part, &g, c->stream));
+    KL(c, HOMO_KC_SETUP, 1, launch_sum_partials(c->part, g, kCases, c->scal + S_FF, c->stream));
+    CK(c, cudaMemcpyAsync(c->hscal + S_FF, c->scal + S_FF, sizeof(double) * kCases, cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    prof_flush(c);
+    double mx = 0.0;
+    for (int k = 0; k < kCases; ++k) mx = std::max(mx, c->hscal[S_FF + k]);
+    for (int k = 0; k < kCases; ++k)
+      if (c->hscal[S_FF + k] <= kLoadResidue * kLoadResidue * mx) {
+        CK(c, cudaMemsetAsync(c->f + 3 * k * c->N, 0, sizeof(float) * 3 * c->N, c->stream));
+        CK(c, cudaMemsetAsync(c->flo + 3 * k * c->N, 0, sizeof(float) * 3 * c->N, c->stream));
+      }
     c->loads_valid = true;
   }
   return HOMO_OK;
