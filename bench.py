@@ -48,9 +48,8 @@ def parse_args(argv=None):
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--sample-n", type=int, default=16, help="cell size of the oracle's CPU sample")
-    ap.add_argument("--sweeps", type=int, default=2,
-                    help="smoothing sweeps before/after coarse correction (0 = library default, 1); "
-                         "2 measured fastest per iteration at 512^3")
+    ap.add_argument("--sweeps", type=int, default=0,
+                    help="smoothing sweeps before/after coarse correction (0 = library default, 1)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
     ap.add_argument("--sym", default="none", choices=["none", "reflect3", "rotate3", "reflect6"],
                     help="symmetry enforced on the sensitivity and the density every step")
