@@ -542,17 +542,15 @@ bool begin_finish(SolveState& s, int* iters_out, double* relres_out) {
 
 bool begin_iteration(SolveState& s, int* iters_out, double* relres_out);
 
+int enq_fold(homo_ctx* c) {
+  KL(c, HOMO_KC_CG_VECTOR, 1, launch_fold(c->u, c->ulo, c->ecyc, c->ecyclo, kPlanes * c->N, c->stream));
+  return HOMO_OK;
+}
+
 // End a cycle: fold the correction into u and recompute the exact residual.
 bool end_cycle(SolveState& s, int* iters_out, double* relres_out) {
   homo_ctx* c = s.c;
-  int rc = HOMO_OK;
-  {
-    auto k = [&]() -> int {
-      KL(c, HOMO_KC_CG_VECTOR, 1, launch_fold(c->u, c->ulo, c->ecyc, c->ecyclo, kPlanes * c->N, c->stream));
-      return HOMO_OK;
-    };
-    rc = k();
-  }
+  const int rc = enq_fold(c);
   if (rc != HOMO_OK) {
     s.status = rc;
     s.phase = SolveState::kDone;
