@@ -20,6 +20,10 @@ The oracle is the plain definition of what the method computes, written from the
 * init.py    - trigonometric density initialisation with sigmoid projection (Sec. 6.2).
 * symmetry.py - orbit averaging under the reflect3 / rotate3 / reflect6 symmetry
                groups (Sec. 6.1).
+* learned.py - the warm-start network: periodic 3x3x3 convolutions with their two
+               derivatives, forward and backward passes with BF16 rounding points,
+               MSE loss and Adam (not part of the paper's method; its readings are in
+               the module header).
 * mg.py      - explicit trilinear prolongation, Galerkin coarse operators R K I and their
                27-block vertex stencils (Sec. 3.3, Eq. 17-18), 8-colour block Gauss-Seidel
                (Eq. 15-16).

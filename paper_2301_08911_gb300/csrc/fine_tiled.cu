@@ -33,8 +33,6 @@ __device__ __forceinline__ void cp_async4(float* smem, const float* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
-
-
 // Per-thread load sites (fixed for every plane): halo site tid and, if it exists,
 // tid + 256, as in-plane offsets gy*n + gx; same for the moduli tile.
 struct Sites {

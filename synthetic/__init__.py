@@ -10,6 +10,8 @@ from .generators import (  # noqa: F401
     splitmix64_uniform,
     uniform_density,
     uniform_field,
+    normal_field,
+    conv_net_parameters,
     smoothed_threshold_density,
     sphere_inclusion_density,
     laminate_density,

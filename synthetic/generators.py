@@ -51,6 +51,27 @@ def uniform_field(count: int, seed: int, lo: float = 0.0, hi: float = 1.0,
     return (lo + (hi - lo) * splitmix64_uniform(seed, count)).astype(dtype)
 
 
+def normal_field(count: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """count i.i.d. standard normal values: Box-Muller on pairs of splitmix64 uniforms
+    (u1 from element 2k, u2 from element 2k+1; 1 - u1 keeps the logarithm finite)."""
+    u = splitmix64_uniform(seed, 2 * count)
+    u1, u2 = 1.0 - u[0::2], u[1::2]
+    return (np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)).astype(dtype)
+
+
+def conv_net_parameters(shapes, seed: int, gains) -> list:
+    """Initial parameters of a stack of 3x3x3 convolutions: for layer l with weight shape
+    (27, c_out, c_in), weights gains[l] * sqrt(2 / (27 c_in)) * N(0, 1) (He scaling; the
+    normal numbers of layer l come from seed + l) and zero biases. Returns [(W, b), ...]
+    as float32 arrays."""
+    out = []
+    for l, (shape, g) in enumerate(zip(shapes, gains)):
+        taps, c_out, c_in = shape
+        w = g * np.sqrt(2.0 / (taps * c_in)) * normal_field(taps * c_out * c_in, seed + l)
+        out.append((w.reshape(shape).astype(np.float32), np.zeros(c_out, np.float32)))
+    return out
+
+
 def uniform_density(n: int, seed: int, lo: float = 0.2, hi: float = 1.0,
                     dtype=np.float32) -> np.ndarray:
     """n^3 i.i.d. densities in [lo, hi)."""
