@@ -67,6 +67,15 @@ def parse_args(argv=None):
                          "{32,48,64,96,128}, volume fraction 0.1-0.5, objectives bulk/shear/poisson), "
                          "each on its own stream, the 6K solves of a step in one lockstep batch")
     ap.add_argument("--graphs", action="store_true", help="replay CG iterations as CUDA graphs")
+    ap.add_argument("--warm-start", default="previous", choices=["previous", "learned", "delta"],
+                    help="start of each solve: the previous iterate (default), the warm-start network's "
+                         "prediction, or the previous iterate plus the predicted change since it")
+    ap.add_argument("--train-n", type=int, default=64, help="cell size of the network's training snapshots")
+    ap.add_argument("--train-cells", type=int, default=3)
+    ap.add_argument("--train-iters", type=int, default=8, help="optimisation iterations per training cell")
+    ap.add_argument("--train-steps", type=int, default=600)
+    ap.add_argument("--train-lr", type=float, default=1e-3)
+    ap.add_argument("--net-blocks", type=int, default=5)
     return ap.parse_args(argv)
 
 
@@ -270,6 +279,10 @@ def config_dict(args):
             "l2": "inputs larger than L2 (18 planes x n^3 fp32 per field)",
             "parallelism": "replicas (one cell per GPU, no collective)",
             "symmetry": args.sym,
+            "warm_start": {"previous": "previous iterate",
+                           "learned": f"warm-start network trained at {args.train_n}^3 (pooled, prolonged)",
+                           "delta": f"previous iterate + predicted change (network trained at {args.train_n}^3)"
+                           }[args.warm_start],
             "precision": ("FP32 storage and arithmetic; double-float displacement and CG correction"
                           if args.precision == "fp32" else
                           "FP32 arithmetic; coarse-level stencils stored in BF16 (symmetrised); "
@@ -301,6 +314,128 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ------------------------------------------------------------------ learned warm start
+def train_warm_start(args, dev, stream):
+    """Snapshots (filtered density, displacement) from short optimisation runs of other
+    seeds at --train-n, then Adam steps of the warm-start network on them. Untimed setup."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2301_08911_gb300 import binding
+    from synthetic import conv_net_parameters, smoothed_threshold_density
+
+    t0 = time.time()
+    nt = args.train_n
+    snaps = []
+    for c in range(args.train_cells):
+        hom = binding.Homogenization(nt, stream=stream.cuda_stream)
+        r = torch.from_numpy(smoothed_threshold_density(nt, args.vf, 1000 + 17 * c)).to(dev)
+        rt, sv, dc = torch.empty_like(r), torch.empty_like(r), torch.empty_like(r)
+        for it in range(args.train_iters):
+            hom.filter(2.0, r, rt)
+            hom.set_density(rt)
+            hom.solve_cases(args.tol, args.max_iters, warm_start=True, raise_on_noconv=False)
+            u = torch.empty(18 * nt ** 3, device=dev)
+            hom.get_displacement(u)
+            snaps.append((rt.clone(), u))
+            _, g = binding.objective(args.objective, hom.CH(), it, 0.8)
+            hom.sensitivity(g, sv)
+            hom.filter(2.0, sv, dc)
+            hom.update(dc, r, args.vf)
+        hom.close()
+    torch.cuda.synchronize(dev)
+    us = np.stack([u.cpu().numpy().astype(np.float64).reshape(6, -1) for _, u in snaps])
+    s_u = np.sqrt((us ** 2).mean(axis=(0, 2))) / nt          # per-case displacement scale per cell size
+    blocks = args.net_blocks
+    shapes = binding.net_layer_shapes(blocks)
+    params = conv_net_parameters(shapes, 4242, [1.0] + [1.0, 0.5] * blocks + [0.1])
+    net = binding.WarmStartNet(blocks, params, stream=stream.cuda_stream)
+    t1 = time.time()
+    losses = []
+    for step in range(args.train_steps):
+        rt, u = snaps[step % len(snaps)]
+        want = step < len(snaps) or step >= args.train_steps - len(snaps)
+        l = net.train_step(nt, rt, u, nt * s_u, args.train_lr, want_loss=want)
+        if want:
+            losses.append(l)
+    torch.cuda.synchronize(dev)
+    k = min(len(snaps), args.train_steps)
+    info = {"train_n": nt, "snapshots": len(snaps), "adam_steps": args.train_steps, "lr": args.train_lr,
+            "blocks": blocks, "channels": binding.NN_CHANNELS,
+            "loss_first_epoch": float(np.mean(losses[:k])), "loss_last_epoch": float(np.mean(losses[-k:])),
+            "snapshot_s": round(t1 - t0, 2), "train_s": round(time.time() - t1, 2),
+            "s_u": [round(float(v), 6) for v in s_u],
+            "data": f"{args.train_cells} cells x {args.train_iters} optimisation iterations at {nt}^3, "
+                    "seeds other than the benchmark cell's"}
+    return net, s_u, info
+
+
+class LearnedStart:
+    """Sets the start of each solve from the warm-start network. The network runs on the
+    density average-pooled to the training cell size (features span the same number of
+    voxels as in training); its prediction is prolonged up the solver's own levels."""
+
+    def __init__(self, args, hom, net, s_u, dev):
+        import torch
+
+        from paper_2301_08911_gb300 import binding
+        self.b = binding
+        self.mode, self.hom, self.net, self.n, self.nt = args.warm_start, hom, net, args.n, args.train_n
+        f = self.n // self.nt
+        if self.n % self.nt or f & (f - 1) or f.bit_length() > hom.num_levels:
+            raise SystemExit("--train-n must be n / 2^k with k below the number of levels")
+        self.L = f.bit_length() - 1                       # level of the training-size grid
+        self.scale = self.n * s_u
+        self.rc = torch.empty(self.nt ** 3, device=dev)
+        self.rc_prev = torch.empty_like(self.rc) if self.mode == "delta" else None
+        self.uc = torch.empty(18 * self.nt ** 3, device=dev)
+        self.lev = [torch.empty(18 * hom.level_size(l) ** 3, device=dev) for l in range(1, self.L)]
+        self.u = torch.empty(18 * self.n ** 3, device=dev)
+        self.have_prev = False
+        self.launches = 0
+
+    def _up(self, add: bool):
+        """uc on level L -> level 0 into self.u (overwrite or accumulate)."""
+        if self.L == 0:
+            return
+        src = self.uc
+        for l in range(self.L - 1, -1, -1):
+            dst = self.u if l == 0 else self.lev[l - 1]
+            if l == 0 and add:
+                self.hom.prolong_add(0, src, dst)
+            else:
+                self.hom.prolong(l, src, dst)
+            src = dst
+
+    def __call__(self, rt):
+        if self.L == 0:
+            self.rc.copy_(rt)                             # same grid: no pooling
+        else:
+            self.b.nn_pool(self.n, self.n // self.nt, rt, self.rc)
+            self.launches += 1
+        target = self.uc if self.L else self.u
+        if self.mode == "learned":
+            self.net.predict(self.nt, self.rc, self.scale, target)
+            self._up(add=False)
+            self.hom.set_displacement(self.u)
+        elif self.have_prev:                             # delta: u_prev + P(rc) - P(rc_prev)
+            if self.L:
+                self.net.predict(self.nt, self.rc, self.scale, self.uc)
+                self.net.predict(self.nt, self.rc_prev, -self.scale, self.uc, accumulate=True)
+                self.hom.get_displacement(self.u)
+                self._up(add=True)
+            else:
+                self.hom.get_displacement(self.u)
+                self.net.predict(self.nt, self.rc, self.scale, self.u, accumulate=True)
+                self.net.predict(self.nt, self.rc_prev, -self.scale, self.u, accumulate=True)
+            self.hom.set_displacement(self.u)
+        if self.mode == "delta":
+            self.rc_prev.copy_(self.rc)
+            self.have_prev = True
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world, local):
     import numpy as np
@@ -322,10 +457,16 @@ def run_ours(args, rank, world, local):
     dc = torch.empty_like(r)
     beta = 0.8
     state = {"it": 0, "cg": [], "relres": []}
+    learned, net_info = None, None
+    if args.warm_start != "previous":
+        net, s_u, net_info = train_warm_start(args, dev, stream)
+        learned = LearnedStart(args, hom, net, s_u, dev)
 
     def step():
         hom.filter(2.0, r, rt)
         hom.set_density(rt)
+        if learned is not None:
+            learned(rt)
         its, rel, _ = hom.solve_cases(args.tol, args.max_iters, warm_start=True, raise_on_noconv=False)
         C = hom.CH()
         f, g = binding.objective(args.objective, C, state["it"], beta)
@@ -360,7 +501,7 @@ def run_ours(args, rank, world, local):
     sampler = ClockSampler(local)
     sampler.start()
     hom.profile(True)
-    launches0 = hom.launch_count
+    launches0 = hom.launch_count + (learned.net.launch_count + learned.launches if learned else 0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
@@ -368,7 +509,7 @@ def run_ours(args, rank, world, local):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
-    launches = hom.launch_count - launches0
+    launches = hom.launch_count + (learned.net.launch_count + learned.launches if learned else 0) - launches0
     n_timed = len(state["cg"])
     prof = hom.profile_read()
     hom.profile(False)
@@ -452,6 +593,8 @@ def run_ours(args, rank, world, local):
                    "max_final_relres": max(state["relres"][:n_timed]) if state["relres"] else None},
         "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
     }
+    if net_info is not None:
+        line["warm_start"] = dict(mode=args.warm_start, **net_info)
     print(json.dumps(line), flush=True)
     return 0
 

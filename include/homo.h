@@ -328,6 +328,8 @@ int homo_get_stencil(homo_ctx* ctx, int level, float* out);
  * R fine; prolong: fine = I coarse (overwrites). */
 int homo_restrict(homo_ctx* ctx, int level, const float* fine, float* coarse);
 int homo_prolong(homo_ctx* ctx, int level, const float* coarse, float* fine);
+/* fine += I coarse (the same prolongation, accumulated). */
+int homo_prolong_add(homo_ctx* ctx, int level, const float* coarse, float* fine);
 
 /* One 8-colour block Gauss-Seidel sweep (Eq. 15-16) on level l, in place on u, colours
  * 0..7 (reverse = 0) or 7..0 (reverse = 1). f, u: device, 6-case layout on level l. */
@@ -376,6 +378,111 @@ long long homo_launch_count(const homo_ctx* ctx);
  * true residual that closes every restart cycle). Copies min(rows, capacity) rows to out
  * (host, 6*capacity doubles) and returns the number of rows (negative on error). */
 int homo_residual_history(const homo_ctx* ctx, double* out, int capacity);
+
+/* ---- Learned warm start --------------------------------------------------------------
+ * Not part of the paper's method, which starts each solve from the previous iterate
+ * (Sec. 3.3). A fully convolutional network maps the filtered density of a cell to the
+ * 18 displacement planes of its 6 load cases; a solve started from its prediction must
+ * still meet the same tolerance, so the zero and previous-iterate starts remain the
+ * reference it is measured against.
+ *
+ * Layouts (device memory; BF16 tensors are uint16 storage, 16-byte aligned):
+ *   activation  x[v*C + c], voxel v = x + n*(y + n*z), C channels (C = 16 for the
+ *               features, HOMO_NN_CHANNELS = 32 for every layer output).
+ *   weights     W[t][o][i] of one layer, t = 9(dz+1) + 3(dy+1) + (dx+1) the tap of offset
+ *               d = (dx,dy,dz) in {-1,0,1}^3, o output channel (32), i input channel.
+ * A layer is the periodic cross-correlation
+ *     y[v,o] = bias[o] + sum_t sum_i W[t,o,i] x[wrap(v + d_t), i]
+ * with BF16 products and FP32 accumulation on the tensor cores.
+ * Network with B residual blocks:
+ *     h0 = relu(conv_in(features)),  t_b = relu(conv1_b(h_{b-1})),
+ *     h_b = relu(conv2_b(t_b) + h_{b-1}),  y = conv_out(h_B),
+ * prediction u[p*N + v] = scale[p/3] * y[v,p] for the 18 planes p (scale[c] = n s_c, s_c a
+ * displacement scale of load case c chosen by the caller, e.g. the RMS of its training
+ * displacements per unit cell size: it balances the 6 cases in the loss).
+ * Features: (rho, rho^2, rho^3, 0, ..., 0).
+ * Parameters (FP32, host order): per layer l = conv_in, conv1_1, conv2_1, ..., conv_out:
+ * W_l (27 * 32 * c_in_l floats, c_in = 16 for conv_in, 32 otherwise) then bias_l (32). */
+#define HOMO_NN_CHANNELS 32
+#define HOMO_NN_FEATURES 16
+#define HOMO_NN_RELU 0     /* out = bf16(relu(acc + bias + res))                         */
+#define HOMO_NN_MASK 1     /* out = bf16((acc + res) * [mask > 0]); bias ignored         */
+#define HOMO_NN_PLANES 2   /* out_planes[p*N + v] = scale[p/3] * (acc + bias), p < 18     */
+#define HOMO_NN_PLANES_ADD 3  /* out_planes[p*N + v] += scale[p/3] * (acc + bias), p < 18 */
+#define HOMO_NN_MSE_SCRATCH 1025   /* doubles of homo_nn_mse's loss buffer           */
+
+/* One layer. x: n^3 x c_in BF16 (c_in 16 or 32; 32 for MASK / PLANES); w: packed BF16
+ * weights [27][32][c_in]; bias: 32 floats or NULL; res, mask: n^3 x 32 BF16 or NULL
+ * (mask required by MASK); out: n^3 x 32 BF16 (RELU, MASK) or out_planes: 18 n^3 floats
+ * (PLANES, PLANES_ADD; then out, res and mask must be NULL); scale: host, 6 per-case
+ * factors of the planes epilogues (NULL = 1). Outputs must not alias inputs.
+ * Asynchronous on stream. HOMO_EINVAL on a bad size, combination or alignment. */
+int homo_nn_conv3d(int n, int c_in, const void* x, const void* w, const float* bias, const void* res,
+                   const void* mask, int epilogue, void* out, float* out_planes, const double* scale,
+                   void* stream);
+
+/* Weight and bias gradients of one layer: dw[t][o][i] = sum_v dy[v,o] x[wrap(v + d_t), i],
+ * db[o] = sum_v dy[v,o] (FP32, summed in a fixed order: deterministic). x: n^3 x c_in
+ * BF16, dy: n^3 x 32 BF16; scratch: device floats, at least homo_nn_wgrad_scratch(n, c_in). */
+size_t homo_nn_wgrad_scratch(int n, int c_in);
+int homo_nn_wgrad(int n, int c_in, const void* x, const void* dy, float* dw, float* db, float* scratch,
+                  size_t scratch_floats, void* stream);
+
+/* Average pooling of a density: out[c] = mean of rho over the factor^3 voxels of coarse
+ * voxel c; rho: n^3 floats, out: (n/factor)^3 floats (device); n divisible by factor. The
+ * network is trained and evaluated on cells whose features span the same number of
+ * voxels; pooling brings a larger cell to that scale. */
+int homo_nn_pool(int n, int factor, const float* rho, float* out, void* stream);
+
+/* Network input features of a filtered density rho (n^3 floats) into x (n^3 x 16 BF16). */
+int homo_nn_features(int n, const float* rho, void* x, void* stream);
+
+/* Loss sum_{v, p<18} (y[p][v] - u[p][v]/scale[p/3])^2 / (18 n^3) of the network output
+ * planes y against solver displacements u (both 18 n^3 floats) into loss[0] (device; loss
+ * holds HOMO_NN_MSE_SCRATCH doubles, the rest is scratch) and its gradient
+ * dy[v][p] = bf16(2 (y - u/scale[p/3]) / (18 n^3)) (n^3 x 32 BF16, zero for p >= 18).
+ * scale: host, 6 positive per-case factors. */
+int homo_nn_mse(int n, const float* y, const float* u, const double* scale, void* dy, double* loss,
+                void* stream);
+
+/* Adam (Kingma and Ba 2015) on count FP32 parameters: m = b1 m + (1-b1) g,
+ * v = b2 v + (1-b2) g^2, w -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps); step >= 1. */
+int homo_nn_adam(size_t count, float* w, const float* g, float* m, float* v, int step, double lr, double beta1,
+                 double beta2, double eps, void* stream);
+
+/* BF16 copies of one layer's FP32 weights w[27][32][c_in]: w_fwd (same layout) and, when
+ * c_in = 32 and w_bwd != NULL, w_bwd[t][i][o] = w[26 - t][o][i], the weights with which
+ * homo_nn_conv3d propagates a gradient back through the layer. */
+int homo_nn_pack(int c_in, const float* w, void* w_fwd, void* w_bwd, void* stream);
+
+/* The network as one object: FP32 master parameters, Adam moments, packed BF16 weights
+ * and activation buffers sized on first use for each grid size. */
+typedef struct homo_net homo_net;
+
+/* Number of FP32 parameters of a network with `blocks` residual blocks (1..16). */
+size_t homo_net_param_count(int blocks);
+/* params: host, homo_net_param_count(blocks) floats in the order above. */
+int homo_net_create(homo_net** out, int blocks, const float* params);
+int homo_net_destroy(homo_net* net);
+const char* homo_net_last_error(const homo_net* net);
+int homo_net_set_stream(homo_net* net, void* cuda_stream);
+/* Copies (host, synchronous) of the parameters and of the gradients of the last train step. */
+int homo_net_get_params(homo_net* net, float* params);
+int homo_net_get_grads(homo_net* net, float* grads);
+/* Predicted displacements for the filtered density rho (device, n^3 floats): u (device,
+ * 18 n^3 floats) = scale[p/3] * y, or u += scale[p/3] * y when accumulate != 0 (scale: host,
+ * 6 factors, any sign). Holds 224 n^3 bytes of activations until released. */
+int homo_net_predict(homo_net* net, int n, const float* rho, const double* scale, float* u, int accumulate);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the loss of homo_nn_mse for the pair
+ * (rho, u) (device); loss: host, nullable (non-NULL synchronises the stream). Holds
+ * (424 + 128 blocks) n^3 bytes of activations plus the weight-gradient scratch until
+ * released. */
+int homo_net_train_step(homo_net* net, int n, const float* rho, const float* u, const double* scale, double lr,
+                        double* loss);
+/* Free the activation buffers. */
+int homo_net_release(homo_net* net);
+/* Kernels this network launched so far. */
+long long homo_net_launch_count(const homo_net* net);
 
 #ifdef __cplusplus
 }

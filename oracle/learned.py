@@ -19,9 +19,11 @@ not part of the paper's method, so every definition below is a reading of its ow
       t_b = relu(conv1_b(h_{b-1})),  h_b = relu(conv2_b(t_b) + h_{b-1})   (b = 1..B)
       y   = conv_out(h_B)   (C output rows; rows 0..17 are the prediction, plane
                              p = 3 case + component, the rest unused)
-  and the displacement u[p, v] = n s_u y[v, p] in voxel units.
+  and the displacement u[p, v] = n s_c y[v, p] in voxel units, c = p // 3 the load
+  case and s_c its displacement scale (per case, so that the loss weighs the 6 cases
+  alike).
 * Loss: L = sum_{v, p < 18} (y[v, p] - T[v, p])^2 / (18 N) with the (mean-free)
-  solver displacement T[v, p] = u[p, v] / (n s_u).
+  solver displacement T[v, p] = u[p, v] / (n s_c).
 * Parameters are updated by Adam (Kingma and Ba 2015, Algorithm 1) in FP32 masters.
 
 With rounding on, the arithmetic mirrors a BF16-storage / wide-accumulate evaluation:
@@ -93,6 +95,13 @@ def conv3d_wgrad(x, dy, n=None):
     n = n or round(x.shape[0] ** (1 / 3))
     dW = np.stack([dy.T @ _shift(x, n, d) for d in tap_offsets()])
     return dW, dy.sum(axis=0)
+
+
+def pool(rho, n: int, f: int):
+    """Average of rho (n^3, x fastest) over each f^3 block: coarse voxel (i, j, k) takes the
+    fine voxels (f i + a, f j + b, f k + c), 0 <= a, b, c < f."""
+    g = np.asarray(rho, dtype=np.float64).reshape(n // f, f, n // f, f, n // f, f)   # (z, c, y, b, x, a)
+    return g.mean(axis=(1, 3, 5)).ravel()
 
 
 def features(rho_t, c_in0: int = 16):
@@ -175,11 +184,17 @@ def adam_step(w, g, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float
     return np.asarray(w, dtype=np.float64) - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def displacement_target(u18, n: int, s_u: float):
-    """Solver planes u (18, N) in voxel units -> voxel-major target T (N, 18) = u^T / (n s_u)."""
-    return np.asarray(u18, dtype=np.float64).reshape(18, -1).T / (n * s_u)
+def _plane_scales(s_u):
+    """Scalar or 6 per-case scales -> 18 per-plane scales (plane p takes case p // 3)."""
+    return np.repeat(np.broadcast_to(np.asarray(s_u, dtype=np.float64), (6,)), 3)
 
 
-def displacement_from_output(y, n: int, s_u: float):
-    """Network output y (N, C) -> displacement planes (18, N) = n s_u y[:, :18]^T."""
-    return n * s_u * np.asarray(y, dtype=np.float64)[:, :18].T
+def displacement_target(u18, n: int, s_u):
+    """Solver planes u (18, N) in voxel units -> voxel-major target T (N, 18),
+    T[v, p] = u[p, v] / (n s_u[p // 3]); s_u scalar or per case."""
+    return np.asarray(u18, dtype=np.float64).reshape(18, -1).T / (n * _plane_scales(s_u))
+
+
+def displacement_from_output(y, n: int, s_u):
+    """Network output y (N, C) -> displacement planes (18, N), u[p, v] = n s_u[p // 3] y[v, p]."""
+    return (n * _plane_scales(s_u))[:, None] * np.asarray(y, dtype=np.float64)[:, :18].T

@@ -79,7 +79,35 @@ SIGNATURES = {
     "homo_solve_batch": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_int, _c_int_p, _c_double_p, _c_int_p]),
     "homo_CH_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_double, _vp, _vp, _vp, _c_double_p, _vp]),
+    # learned warm start
+    "homo_nn_conv3d": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_int, _vp, _vp,
+                                      _c_double_p, _vp]),
+    "homo_nn_wgrad_scratch": (ctypes.c_size_t, [ctypes.c_int, ctypes.c_int]),
+    "homo_nn_wgrad": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, ctypes.c_size_t, _vp]),
+    "homo_nn_features": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp]),
+    "homo_nn_mse": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _c_double_p, _vp, _vp, _vp]),
+    "homo_nn_adam": (ctypes.c_int, [ctypes.c_size_t, _vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_double, _vp]),
+    "homo_nn_pack": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp]),
+    "homo_net_param_count": (ctypes.c_size_t, [ctypes.c_int]),
+    "homo_net_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, _vp]),
+    "homo_net_destroy": (ctypes.c_int, [_vp]),
+    "homo_net_last_error": (ctypes.c_char_p, [_vp]),
+    "homo_net_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "homo_net_get_params": (ctypes.c_int, [_vp, _vp]),
+    "homo_net_get_grads": (ctypes.c_int, [_vp, _vp]),
+    "homo_net_predict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _c_double_p, _vp, ctypes.c_int]),
+    "homo_nn_pool": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
+    "homo_prolong_add": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "homo_net_train_step": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_double_p, ctypes.c_double,
+                                           _c_double_p]),
+    "homo_net_release": (ctypes.c_int, [_vp]),
+    "homo_net_launch_count": (ctypes.c_longlong, [_vp]),
 }
+
+NN_CHANNELS, NN_FEATURES = 32, 16
+NN_EPILOGUES = {"relu": 0, "mask": 1, "planes": 2, "planes_add": 3}
+NN_MSE_SCRATCH = 1025
 
 KERNEL_CLASSES = 15
 
@@ -273,6 +301,9 @@ class Homogenization:
     def get_stencil(self, level: int, out):
         self._check(self.lib.homo_get_stencil(self.h, level, _vp(_ptr(out))))
 
+    def prolong_add(self, level: int, coarse, fine):
+        self._check(self.lib.homo_prolong_add(self.h, level, _vp(_ptr(coarse)), _vp(_ptr(fine))))
+
     def restrict(self, level: int, fine, coarse):
         self._check(self.lib.homo_restrict(self.h, level, _vp(_ptr(fine)), _vp(_ptr(coarse))))
 
@@ -316,3 +347,168 @@ class Homogenization:
         buf = (ctypes.c_double * max(6 * rows, 1))()
         self.lib.homo_residual_history(self.h, buf, rows)
         return np.frombuffer(buf, dtype=np.float64)[:6 * rows].reshape(rows, 6).copy()
+
+
+# ---------------------------------------------------------------- learned warm start
+def _dptr(t) -> int:
+    """Device pointer of a contiguous CUDA tensor of any dtype (BF16 activations included)."""
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _opt(t):
+    return _vp(_dptr(t)) if t is not None else None
+
+
+def _stream_of(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else getattr(stream, "cuda_stream", stream)
+
+
+def _scale6(scale):
+    """A scalar or 6 per-case factors -> ctypes double[6]."""
+    v = np.broadcast_to(np.asarray(scale, dtype=np.float64), (6,))
+    return (ctypes.c_double * 6)(*v.tolist())
+
+
+def _nn_check(st: int, what: str):
+    if st != HOMO_OK:
+        raise HomoError(st, what)
+
+
+def nn_conv3d(n: int, c_in: int, x, w, bias=None, res=None, mask=None, epilogue: str = "relu", out=None,
+              out_planes=None, scale=1.0, stream=None):
+    """One network layer (homo_nn_conv3d); tensors are CUDA tensors in the header's layouts;
+    scale: scalar or 6 per-case factors of the planes epilogues."""
+    lib = load_library()
+    _nn_check(lib.homo_nn_conv3d(n, c_in, _vp(_dptr(x)), _vp(_dptr(w)), _opt(bias), _opt(res), _opt(mask),
+                                 NN_EPILOGUES[epilogue], _opt(out), _opt(out_planes), _scale6(scale),
+                                 _vp(_stream_of(stream))), "homo_nn_conv3d")
+
+
+def nn_wgrad_scratch(n: int, c_in: int) -> int:
+    return int(load_library().homo_nn_wgrad_scratch(n, c_in))
+
+
+def nn_wgrad(n: int, c_in: int, x, dy, dw, db, scratch, stream=None):
+    lib = load_library()
+    _nn_check(lib.homo_nn_wgrad(n, c_in, _vp(_dptr(x)), _vp(_dptr(dy)), _vp(_dptr(dw)), _vp(_dptr(db)),
+                                _vp(_dptr(scratch)), scratch.numel(), _vp(_stream_of(stream))), "homo_nn_wgrad")
+
+
+def nn_features(n: int, rho, x, stream=None):
+    _nn_check(load_library().homo_nn_features(n, _vp(_dptr(rho)), _vp(_dptr(x)), _vp(_stream_of(stream))),
+              "homo_nn_features")
+
+
+def nn_pool(n: int, factor: int, rho, out, stream=None):
+    _nn_check(load_library().homo_nn_pool(n, factor, _vp(_dptr(rho)), _vp(_dptr(out)), _vp(_stream_of(stream))),
+              "homo_nn_pool")
+
+
+def nn_mse(n: int, y, u, scale, dy, loss, stream=None):
+    _nn_check(load_library().homo_nn_mse(n, _vp(_dptr(y)), _vp(_dptr(u)), _scale6(scale), _vp(_dptr(dy)),
+                                         _vp(_dptr(loss)), _vp(_stream_of(stream))), "homo_nn_mse")
+
+
+def nn_adam(w, g, m, v, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+            stream=None):
+    _nn_check(load_library().homo_nn_adam(w.numel(), _vp(_dptr(w)), _vp(_dptr(g)), _vp(_dptr(m)),
+                                          _vp(_dptr(v)), step, lr, beta1, beta2, eps, _vp(_stream_of(stream))),
+              "homo_nn_adam")
+
+
+def nn_pack(c_in: int, w, w_fwd, w_bwd=None, stream=None):
+    _nn_check(load_library().homo_nn_pack(c_in, _vp(_dptr(w)), _vp(_dptr(w_fwd)), _opt(w_bwd),
+                                          _vp(_stream_of(stream))), "homo_nn_pack")
+
+
+def net_layer_shapes(blocks: int):
+    """Weight shapes (27, 32, c_in) of the layers in parameter order."""
+    return [(27, NN_CHANNELS, NN_FEATURES)] + [(27, NN_CHANNELS, NN_CHANNELS)] * (2 * blocks + 1)
+
+
+def net_flatten(params) -> np.ndarray:
+    """[(W, b), ...] -> the flat FP32 parameter vector of homo_net_create."""
+    return np.concatenate([np.concatenate([np.asarray(W, np.float32).ravel(), np.asarray(b, np.float32).ravel()])
+                           for W, b in params])
+
+
+def net_unflatten(flat, blocks: int):
+    out, off = [], 0
+    for shape in net_layer_shapes(blocks):
+        nw = int(np.prod(shape))
+        out.append((flat[off:off + nw].reshape(shape), flat[off + nw:off + nw + NN_CHANNELS]))
+        off += nw + NN_CHANNELS
+    return out
+
+
+class WarmStartNet:
+    """The warm-start network (homo_net): predicts the 18 displacement planes of a cell
+    from its filtered density; trained by Adam on (density, solver displacement) pairs."""
+
+    def __init__(self, blocks: int, params, stream=None):
+        self.lib = load_library()
+        flat = np.ascontiguousarray(params if isinstance(params, np.ndarray) else net_flatten(params),
+                                    dtype=np.float32)
+        count = int(self.lib.homo_net_param_count(blocks))
+        if flat.size != count:
+            raise ValueError(f"expected {count} parameters, got {flat.size}")
+        h = _vp()
+        st = self.lib.homo_net_create(ctypes.byref(h), blocks, flat.ctypes.data_as(_vp))
+        if st != HOMO_OK:
+            raise HomoError(st, "homo_net_create")
+        self.h = h
+        self.blocks = blocks
+        self.count = count
+        self.set_stream(stream)
+
+    def _check(self, st: int):
+        if st != HOMO_OK:
+            raise HomoError(st, self.lib.homo_net_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.homo_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        self._check(self.lib.homo_net_set_stream(self.h, _vp(_stream_of(stream))))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.count, np.float32)
+        self._check(self.lib.homo_net_get_params(self.h, out.ctypes.data_as(_vp)))
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.count, np.float32)
+        self._check(self.lib.homo_net_get_grads(self.h, out.ctypes.data_as(_vp)))
+        return out
+
+    def predict(self, n: int, rho, scale, u, accumulate: bool = False):
+        """u (CUDA float32, 18 n^3) = scale[case] * network(rho) (or += when accumulate) for
+        the filtered density rho (n^3); scale: scalar or 6 per-case factors."""
+        self._check(self.lib.homo_net_predict(self.h, n, _vp(_ptr(rho)), _scale6(scale), _vp(_ptr(u)),
+                                              int(accumulate)))
+
+    def train_step(self, n: int, rho, u, scale, lr: float, want_loss: bool = True):
+        loss = ctypes.c_double()
+        self._check(self.lib.homo_net_train_step(self.h, n, _vp(_ptr(rho)), _vp(_ptr(u)), _scale6(scale), lr,
+                                                 ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def release(self):
+        self._check(self.lib.homo_net_release(self.h))
+
+    @property
+    def launch_count(self) -> int:
+        return self.lib.homo_net_launch_count(self.h)

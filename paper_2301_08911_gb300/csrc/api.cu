@@ -1170,6 +1170,12 @@ int homo_prolong(homo_ctx* ctx, int level, const float* coarse, float* fine) {
   return HOMO_OK;
 }
 
+int homo_prolong_add(homo_ctx* ctx, int level, const float* coarse, float* fine) {
+  if (!ctx || !fine || !coarse || level < 0 || level + 1 >= ctx->nlev) return HOMO_EINVAL;
+  KL(ctx, HOMO_KC_TRANSFER, 1, launch_prolong_add(ctx->lev[level].n, coarse, fine, 0, ctx->stream));
+  return HOMO_OK;
+}
+
 int homo_smooth(homo_ctx* ctx, int level, int reverse, const float* f, float* u) {
   if (!ctx || !f || !u || level < 0 || level >= ctx->nlev) return HOMO_EINVAL;
   if (ctx->lev[level].n % 2 != 0) return set_err(ctx, HOMO_EINVAL, "smoothing needs an even level size");

@@ -248,6 +248,22 @@ cudaError_t launch_stencil_export(const Level& L, float* out, cudaStream_t s);
 // level-0 stencil (243 planes, colour-blocked when n is even) built from E and K0
 cudaError_t launch_fine_stencil(const homo_ctx* c, const Level& L0);
 
+// ---- launchers (learned.cu): warm-start network layers (layouts in homo.h) ----
+// scale: 6 per-case factors of the planes epilogues (host, nullable = 1)
+cudaError_t nn_conv3d(int n, int cin, const void* x, const void* w, const float* bias, const void* res,
+                      const void* mask, int epi, void* out, float* outf, const double* scale, cudaStream_t s);
+// scratch: homo_nn_wgrad_scratch(n, cin) floats
+cudaError_t nn_wgrad(int n, int cin, const void* x, const void* dy, float* dw, float* db, float* scratch,
+                     cudaStream_t s);
+cudaError_t nn_features(int n, const float* rho, void* x, cudaStream_t s);
+// part: HOMO_NN_MSE_SCRATCH - 1 doubles; *nblk partials written
+cudaError_t nn_mse(int n, const float* y, const float* u, const double* scale, void* dy, double* part, int* nblk,
+                   cudaStream_t s);
+cudaError_t nn_adam(size_t count, float* w, const float* g, float* m, float* v, int step, double lr, double b1,
+                    double b2, double eps, cudaStream_t s);
+cudaError_t nn_pack(int cin, const float* w, void* wf, void* wb, cudaStream_t s);
+cudaError_t nn_pool(int n, int f, const float* rho, float* out, cudaStream_t s);
+
 // ---- launchers (vec.cu) ----
 int reduce_grid(size_t n_items);
 cudaError_t launch_sum_partials(const double* part, int nblk, int nv, double* out,

@@ -91,3 +91,27 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
         assert lib.homo_last_error(None)
     assert lib.homo_destroy(None) == binding.HOMO_OK
     assert lib.homo_status_string(binding.HOMO_ENOCONV).decode().startswith("not converged")
+
+
+def test_warm_start_network_host_checks(lib):
+    """Parameter count of the network layout, and argument checks that return before any
+    CUDA call (nothing is launched)."""
+    for blocks in (1, 5, 16):
+        want = sum(int(np.prod(s)) + 32 for s in binding.net_layer_shapes(blocks))
+        assert lib.homo_net_param_count(blocks) == want
+    assert lib.homo_net_param_count(0) == 0 and lib.homo_net_param_count(17) == 0
+    assert lib.homo_nn_wgrad_scratch(16, 24) == 0
+    p = ctypes.c_void_p(4096)                       # aligned, never dereferenced
+    E = binding.HOMO_EINVAL
+    conv = lib.homo_nn_conv3d
+    assert conv(8, 24, p, p, None, None, None, 0, p, None, None, None) == E      # c_in
+    assert conv(8, 16, p, p, None, None, p, 1, p, None, None, None) == E         # mask needs c_in 32
+    assert conv(8, 32, p, p, None, None, None, 1, p, None, None, None) == E      # mask missing
+    assert conv(8, 32, p, p, None, p, None, 2, None, p, None, None) == E         # planes with residual
+    assert conv(8, 32, ctypes.c_void_p(4100), p, None, None, None, 0, p, None, None, None) == E   # alignment
+    assert conv(0, 32, p, p, None, None, None, 0, p, None, None, None) == E      # size
+    assert conv(8, 32, p, p, None, None, None, 7, p, None, None, None) == E      # epilogue
+    assert lib.homo_nn_pool(10, 3, p, p, None) == E
+    assert lib.homo_nn_adam(4, p, p, p, p, 0, 1e-3, 0.9, 0.999, 1e-8, None) == E
+    assert lib.homo_nn_pack(16, p, p, p, None) == E                             # no transposed copy for c_in 16
+    assert lib.homo_net_create(None, 5, p) == E

@@ -158,7 +158,21 @@ def test_mse_loss_gradient_and_displacement_maps():
     eps = 1e-6
     fd = (L.mse_loss(y + eps * d, T)[0] - L.mse_loss(y - eps * d, T)[0]) / (2 * eps)
     assert abs(fd - float((g * d).sum())) < 1e-8
-    n, s = 2, 0.05
+    n, s = 2, np.array([0.05, 0.1, 0.2, 0.03, 0.07, 0.5])
     u = _rand((18, n ** 3), 44)
     T2 = L.displacement_target(u, n, s)
+    assert np.allclose(T2[:, 4], u[4] / (n * s[1])) and np.allclose(T2[:, 17], u[17] / (n * s[5]))
     assert np.allclose(L.displacement_from_output(np.hstack([T2, np.zeros((n ** 3, 14))]), n, s), u)
+
+
+def test_pool_by_brute_force():
+    n, f = 6, 3
+    rho = uniform_field(n ** 3, 51, 0.0, 1.0, np.float64)
+    got = L.pool(rho, n, f)
+    g = rho.reshape(n, n, n)                                 # (z, y, x)
+    for k in range(2):
+        for j in range(2):
+            for i in range(2):
+                want = np.mean([g[f * k + c, f * j + b, f * i + a]
+                                for a in range(f) for b in range(f) for c in range(f)])
+                assert abs(got[i + 2 * (j + 2 * k)] - want) < 1e-15
