@@ -361,11 +361,32 @@ def train_warm_start(args, dev, stream):
         if want:
             losses.append(l)
     torch.cuda.synchronize(dev)
+    # one network forward at the training size, timed with CUDA events on its stream
+    u_tmp = torch.empty(18 * nt ** 3, device=dev)
+    net.predict(nt, snaps[0][0], nt * s_u, u_tmp)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        net.predict(nt, snaps[0][0], nt * s_u, u_tmp)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms = e0.elapsed_time(e1) / reps
+    conv_flop = 2 * 27 * binding.NN_CHANNELS * (binding.NN_FEATURES + (2 * blocks + 1) * binding.NN_CHANNELS)
+    fwd_tflops = conv_flop * nt ** 3 / (fwd_ms * 1e-3) / 1e12
+    bf16_peak = None
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        with open(pk) as fh:
+            bf16_peak = json.load(fh).get("bf16_tflops")
     k = min(len(snaps), args.train_steps)
     info = {"train_n": nt, "snapshots": len(snaps), "adam_steps": args.train_steps, "lr": args.train_lr,
             "blocks": blocks, "channels": binding.NN_CHANNELS,
             "loss_first_epoch": float(np.mean(losses[:k])), "loss_last_epoch": float(np.mean(losses[-k:])),
-            "snapshot_s": round(t1 - t0, 2), "train_s": round(time.time() - t1, 2),
+            "forward_ms": round(fwd_ms, 4), "forward_conv_flop_per_voxel": conv_flop,
+            "forward_tflops": round(fwd_tflops, 2),
+            "forward_frac_of_measured_bf16": (round(fwd_tflops / bf16_peak, 4) if bf16_peak else None),
+            "snapshot_s": round(t1 - t0, 2), "train_s": round(time.time() - t1, 3),
             "s_u": [round(float(v), 6) for v in s_u],
             "data": f"{args.train_cells} cells x {args.train_iters} optimisation iterations at {nt}^3, "
                     "seeds other than the benchmark cell's"}
