@@ -67,6 +67,8 @@ def parse_args(argv=None):
                          "{32,48,64,96,128}, volume fraction 0.1-0.5, objectives bulk/shear/poisson), "
                          "each on its own stream, the 6K solves of a step in one lockstep batch")
     ap.add_argument("--graphs", action="store_true", help="replay CG iterations as CUDA graphs")
+    ap.add_argument("--autotune", action="store_true",
+                    help="time the fine Gauss-Seidel variants per cell size before the run and use the fastest")
     ap.add_argument("--warm-start", default="previous", choices=["previous", "learned", "delta"],
                     help="start of each solve: the previous iterate (default), the warm-start network's "
                          "prediction, or the previous iterate plus the predicted change since it")
@@ -478,6 +480,13 @@ def run_ours(args, rank, world, local):
     dc = torch.empty_like(r)
     beta = 0.8
     state = {"it": 0, "cg": [], "relres": []}
+    tuning = None
+    if args.autotune:
+        hom.filter(2.0, r, rt)
+        hom.set_density(rt)
+        choice, times = hom.autotune(retime=True)
+        tuning = {"cases_per_thread": choice[0], "threads_per_block": choice[1],
+                  "ms_per_sweep": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times.items()}}
     learned, net_info = None, None
     if args.warm_start != "previous":
         net, s_u, net_info = train_warm_start(args, dev, stream)
@@ -616,6 +625,8 @@ def run_ours(args, rank, world, local):
     }
     if net_info is not None:
         line["warm_start"] = dict(mode=args.warm_start, **net_info)
+    if tuning is not None:
+        line["autotune"] = tuning
     print(json.dumps(line), flush=True)
     return 0
 
@@ -668,6 +679,16 @@ def run_batch(args, rank, world, local):
         cells.append({"hom": hom, "stream": st, "n": n, "vf": vf, "obj": obj, "r": r,
                       "rt": torch.empty_like(r), "s": torch.empty_like(r), "dc": torch.empty_like(r)})
     torch.cuda.synchronize()
+    tuning = {}
+    if args.autotune:
+        for c in cells:
+            c["hom"].filter(2.0, c["r"], c["rt"])
+            c["hom"].set_density(c["rt"])
+            choice, times = c["hom"].autotune()
+            if times:
+                tuning[c["n"]] = {"cases_per_thread": choice[0], "threads_per_block": choice[1],
+                                  "ms_per_sweep": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times.items()}}
+        torch.cuda.synchronize()
     it = {"k": 0, "cg": []}
 
     def step():
@@ -709,7 +730,8 @@ def run_batch(args, rank, world, local):
                                    + (", CG iterations as CUDA graphs" if args.graphs else ""),
                        "cells": args.batch, "elements_per_gpu": elements,
                        "sizes": sorted({n for n, _, _, _ in specs}), "graphs": args.graphs,
-                       "timing": "host clock around device-synchronised steps (one stream per cell)"},
+                       "timing": "host clock around device-synchronised steps (one stream per cell)",
+                       "autotune": tuning or None},
             "gpu_launches": launches, "solver": {"max_cg_iterations_per_step": it["cg"][-args.steps:]}}
     print(json.dumps(line), flush=True)
     return 0

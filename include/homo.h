@@ -331,6 +331,21 @@ int homo_prolong(homo_ctx* ctx, int level, const float* coarse, float* fine);
 /* fine += I coarse (the same prolongation, accumulated). */
 int homo_prolong_add(homo_ctx* ctx, int level, const float* coarse, float* fine);
 
+/* ---- Tuning ----
+ * The finest-level Gauss-Seidel pass (Eq. 15-16) is compiled in four variants: 3 or 6
+ * load cases per thread (3: the cases are split over two thread groups, each rebuilding
+ * the coupling blocks; 6: blocks built once, more registers) times 128 or 256 threads
+ * per block. All four compute bitwise the same result; which is fastest depends on the
+ * grid size. homo_set_tuning selects one (default 3, 256). homo_autotune times one
+ * symmetric sweep pair of each on the context's own moduli and loads (needs a density;
+ * uses the solver's scratch, so call it between solves), selects the fastest and caches
+ * the choice per grid size for the process; flags HOMO_TUNE_RETIME ignores the cache.
+ * Outputs (host, nullable): the chosen variant; ms: 4 times per sweep of the variants
+ * (3,256), (3,128), (6,256), (6,128), -1 when the choice came from the cache. */
+#define HOMO_TUNE_RETIME 1
+int homo_set_tuning(homo_ctx* ctx, int gs_cases, int gs_block);
+int homo_autotune(homo_ctx* ctx, int flags, int* gs_cases, int* gs_block, double* ms);
+
 /* One 8-colour block Gauss-Seidel sweep (Eq. 15-16) on level l, in place on u, colours
  * 0..7 (reverse = 0) or 7..0 (reverse = 1). f, u: device, 6-case layout on level l. */
 int homo_smooth(homo_ctx* ctx, int level, int reverse, const float* f, float* u);

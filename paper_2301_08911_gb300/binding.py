@@ -99,6 +99,8 @@ SIGNATURES = {
     "homo_net_predict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _c_double_p, _vp, ctypes.c_int]),
     "homo_nn_pool": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]),
     "homo_prolong_add": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
+    "homo_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
+    "homo_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_int_p, _c_double_p]),
     "homo_net_train_step": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_double_p, ctypes.c_double,
                                            _c_double_p]),
     "homo_net_release": (ctypes.c_int, [_vp]),
@@ -315,6 +317,21 @@ class Homogenization:
 
     def vcycle(self, r, z):
         self._check(self.lib.homo_vcycle(self.h, _vp(_ptr(r)), _vp(_ptr(z))))
+
+    # ---------------------------------------------------------------- tuning
+    GS_VARIANTS = ((3, 256), (3, 128), (6, 256), (6, 128))
+
+    def set_tuning(self, gs_cases: int, gs_block: int):
+        self._check(self.lib.homo_set_tuning(self.h, gs_cases, gs_block))
+
+    def autotune(self, retime: bool = False):
+        """Time the fine Gauss-Seidel variants on this cell, select the fastest. Returns
+        ((cases, block), {variant: ms per sweep}) (empty timings when cached for the size)."""
+        c, b = ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 4)()
+        self._check(self.lib.homo_autotune(self.h, int(retime), ctypes.byref(c), ctypes.byref(b), ms))
+        times = {v: ms[k] for k, v in enumerate(self.GS_VARIANTS) if ms[k] >= 0}
+        return (c.value, b.value), times
 
     # ---------------------------------------------------------------- measurement
     def profile(self, enable: bool):

@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -1167,6 +1169,83 @@ int homo_restrict(homo_ctx* ctx, int level, const float* fine, float* coarse) {
 int homo_prolong(homo_ctx* ctx, int level, const float* coarse, float* fine) {
   if (!ctx || !fine || !coarse || level < 0 || level + 1 >= ctx->nlev) return HOMO_EINVAL;
   KL(ctx, HOMO_KC_TRANSFER, 1, launch_prolong_add(ctx->lev[level].n, coarse, fine, 1, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_set_tuning(homo_ctx* ctx, int gs_cases, int gs_block) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!gs_variant_ok(gs_cases, gs_block)) return set_err(ctx, HOMO_EINVAL, "no such Gauss-Seidel variant");
+  if (gs_cases != ctx->gs_cases || gs_block != ctx->gs_block) drop_graphs(ctx);
+  ctx->gs_cases = gs_cases;
+  ctx->gs_block = gs_block;
+  return HOMO_OK;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<int, std::pair<int, int>> g_tune_cache;   // grid size -> (cases, block)
+}  // namespace
+
+int homo_autotune(homo_ctx* ctx, int flags, int* gs_cases, int* gs_block, double* ms) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!ctx->density_set) return set_err(ctx, HOMO_ESTATE, "homo_autotune needs a density");
+  static const int kVar[4][2] = {{3, 256}, {3, 128}, {6, 256}, {6, 128}};
+  if (ms)
+    for (int k = 0; k < 4; ++k) ms[k] = -1.0;
+  int best = -1;
+  if (!(flags & HOMO_TUNE_RETIME)) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(ctx->n);
+    if (it != g_tune_cache.end())
+      for (int k = 0; k < 4; ++k)
+        if (kVar[k][0] == it->second.first && kVar[k][1] == it->second.second) best = k;
+  }
+  if (best < 0) {
+    // time one symmetric sweep pair (16 colour passes) of each variant on the context's
+    // own moduli and loads, into the CG scratch vector z (free between solves)
+    RET(ensure_loads(ctx));
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      return set_err(ctx, HOMO_ECUDA, "homo_autotune: cudaEventCreate failed");
+    }
+    const int save_c = ctx->gs_cases, save_b = ctx->gs_block;
+    double best_ms = 0.0;
+    int rc = HOMO_OK;
+    for (int k = 0; k < 4 && rc == HOMO_OK; ++k) {
+      ctx->gs_cases = kVar[k][0];
+      ctx->gs_block = kVar[k][1];
+      rc = smooth_level(ctx, 0, false, ctx->f, ctx->z, true);            // warm-up, from zero
+      if (rc != HOMO_OK) break;
+      if (cudaEventRecord(a, ctx->stream) != cudaSuccess) { rc = HOMO_ECUDA; break; }
+      for (int rep = 0; rep < 2 && rc == HOMO_OK; ++rep) {
+        rc = smooth_level(ctx, 0, false, ctx->f, ctx->z);
+        if (rc == HOMO_OK) rc = smooth_level(ctx, 0, true, ctx->f, ctx->z);
+      }
+      if (rc != HOMO_OK) break;
+      float t = 0.f;
+      if (cudaEventRecord(b, ctx->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+          cudaEventElapsedTime(&t, a, b) != cudaSuccess) {
+        rc = HOMO_ECUDA;
+        break;
+      }
+      if (ms) ms[k] = t / 2.0;
+      if (best < 0 || t < best_ms) {
+        best = k;
+        best_ms = t;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->gs_cases = save_c;
+    ctx->gs_block = save_b;
+    if (rc != HOMO_OK) return rc == HOMO_ECUDA ? set_err(ctx, rc, "homo_autotune: timing failed") : rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[ctx->n] = {kVar[best][0], kVar[best][1]};
+  }
+  RET(homo_set_tuning(ctx, kVar[best][0], kVar[best][1]));
+  if (gs_cases) *gs_cases = kVar[best][0];
+  if (gs_block) *gs_block = kVar[best][1];
   return HOMO_OK;
 }
 

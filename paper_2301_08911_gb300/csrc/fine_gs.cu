@@ -11,15 +11,16 @@ namespace {
 // colour, so its value is not written during the pass (read through the read-only
 // path). first != 0: first sweep from u = 0 in colour order 0..7, where neighbours of a
 // higher colour still hold zero and are skipped (u need not be cleared beforehand).
-// The load cases are split over blockIdx.y in groups of kGsCases: the blocks A_d are
-// rebuilt per group, which keeps registers low and puts more loads in flight.
-constexpr int kGsCases = 3;
-
-__global__ void __launch_bounds__(256, 4) k_fine_gs(const __grid_constant__ KeParam K,
-                                                 const float* __restrict__ E,
-                                                 const float* __restrict__ f,
-                                                 float* __restrict__ u, int n, int colour,
-                                                 int first, const double* __restrict__ fmean) {
+// The load cases are split over blockIdx.y in groups of CASES (3: the blocks A_d are
+// rebuilt per group, which keeps registers low and puts more loads in flight; 6: built
+// once). Every variant (CASES, BLOCK) performs the same arithmetic per vertex and case in
+// the same order, so all give bitwise the same result; homo_autotune picks the fastest
+// for a grid size.
+template <int CASES, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (CASES == 3 ? 1024 : 512) / BLOCK)
+    k_fine_gs(const __grid_constant__ KeParam K, const float* __restrict__ E, const float* __restrict__ f,
+              float* __restrict__ u, int n, int colour, int first, const double* __restrict__ fmean) {
+  constexpr int kGsCases = CASES;
   const size_t N = static_cast<size_t>(n) * n * n;
   const int h = n >> 1;
   const size_t Nh = static_cast<size_t>(h) * h * h;
@@ -65,14 +66,25 @@ __global__ void __launch_bounds__(256, 4) k_fine_gs(const __grid_constant__ KePa
   }
 }
 
+template <int CASES, int BLOCK>
+cudaError_t gs_launch(const homo_ctx* c, int colour, const float* f, float* u, int first, const double* fmean) {
+  const size_t h = static_cast<size_t>(c->n / 2);
+  const dim3 grid(grid_for(h * h * h, BLOCK), kCases / CASES);
+  k_fine_gs<CASES, BLOCK><<<grid, BLOCK, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour, first, fmean);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+bool gs_variant_ok(int cases, int block) { return (cases == 3 || cases == 6) && (block == 128 || block == 256); }
 
 cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first,
                            const double* fmean) {
-  const size_t h = static_cast<size_t>(c->n / 2);
-  const dim3 grid(grid_for(h * h * h, 256), kCases / kGsCases);
-  k_fine_gs<<<grid, 256, 0, c->stream>>>(c->ke, c->E, f, u, c->n, colour, first, fmean);
-  return cudaGetLastError();
+  if (c->gs_cases == 6)
+    return c->gs_block == 128 ? gs_launch<6, 128>(c, colour, f, u, first, fmean)
+                              : gs_launch<6, 256>(c, colour, f, u, first, fmean);
+  return c->gs_block == 128 ? gs_launch<3, 128>(c, colour, f, u, first, fmean)
+                            : gs_launch<3, 256>(c, colour, f, u, first, fmean);
 }
 
 }  // namespace homo

@@ -169,6 +169,10 @@ struct homo_ctx {
 
   // CUDA graphs of one CG iteration (index: first iteration of a cycle or not), captured
   // on first use after the hierarchy is built and dropped when it is rebuilt
+  // fine Gauss-Seidel variant: load cases per thread (3 or 6) and threads per block
+  // (128 or 256); set by homo_set_tuning / homo_autotune
+  int gs_cases = 3, gs_block = 256;
+
   cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};
   long long cg_graph_launches[2] = {0, 0};   // kernels per replay
   double cg_graph_tol = 0.0;                  // inner tolerance captured in the graphs
@@ -227,6 +231,8 @@ cudaError_t launch_fine_residual(const homo_ctx* c, const float* b, const float*
 // means subtracted from f, or null
 cudaError_t launch_fine_gs(const homo_ctx* c, int colour, const float* f, float* u, int first,
                            const double* fmean);
+// (cases, block) is a compiled variant of the fine Gauss-Seidel kernel
+bool gs_variant_ok(int cases, int block);
 cudaError_t launch_fine_elem(const homo_ctx* c, int mode, const double* g36, float* sens,
                              double* part, int* grid_out);
 

@@ -115,3 +115,9 @@ def test_warm_start_network_host_checks(lib):
     assert lib.homo_nn_adam(4, p, p, p, p, 0, 1e-3, 0.9, 0.999, 1e-8, None) == E
     assert lib.homo_nn_pack(16, p, p, p, None) == E                             # no transposed copy for c_in 16
     assert lib.homo_net_create(None, 5, p) == E
+
+
+def test_tuning_argument_checks(lib):
+    """Host-side checks of the tuning entry points (no context, nothing launched)."""
+    assert lib.homo_set_tuning(None, 3, 256) == binding.HOMO_EINVAL
+    assert lib.homo_autotune(None, 0, None, None, None) == binding.HOMO_EINVAL

@@ -105,3 +105,38 @@ def test_batch_argument_errors(B):
     with pytest.raises(B.HomoError) as e:
         B.solve_batch([hom, hom], 1e-6)
     assert e.value.status == B.HOMO_EINVAL
+
+
+def test_gauss_seidel_variants_are_bitwise_equal_and_autotune_picks_the_fastest(B):
+    """The four compiled Gauss-Seidel variants (3 or 6 cases per thread, 128 or 256 threads)
+    give bitwise the same solve; homo_autotune selects the fastest it timed and caches the
+    choice for the grid size."""
+    n = 24
+    rho = _density(n, 3)
+    ref = None
+    for cases, block in B.Homogenization.GS_VARIANTS:
+        hom = B.Homogenization(n)
+        _set(hom, rho)
+        hom.set_tuning(cases, block)
+        its, _, _ = hom.solve_cases(1e-7, 400, warm_start=False)
+        u = torch.empty(18 * n ** 3, device="cuda")
+        hom.get_displacement(u)
+        got = (list(its), hom.CH(), u.cpu().numpy())
+        if ref is None:
+            ref = got
+        else:
+            assert got[0] == ref[0], (cases, block)
+            assert np.array_equal(got[1], ref[1]) and np.array_equal(got[2], ref[2]), (cases, block)
+    hom = B.Homogenization(n)
+    _set(hom, rho)
+    choice, times = hom.autotune(retime=True)
+    assert choice in B.Homogenization.GS_VARIANTS and len(times) == 4
+    assert all(t > 0 for t in times.values()) and times[choice] == min(times.values())
+    hom2 = B.Homogenization(n)
+    _set(hom2, rho)
+    choice2, times2 = hom2.autotune()
+    assert choice2 == choice and times2 == {}                # from the per-size cache
+    its, _, _ = hom2.solve_cases(1e-7, 400, warm_start=False)
+    assert list(its) == ref[0] and np.array_equal(hom2.CH(), ref[1])
+    with pytest.raises(B.HomoError):
+        hom2.set_tuning(4, 256)
