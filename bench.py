@@ -434,28 +434,29 @@ class LearnedStart:
 
     def __call__(self, rt):
         if self.L == 0:
-            self.rc.copy_(rt)                             # same grid: no pooling
+            rc = rt                                       # same grid: no pooling
         else:
             self.b.nn_pool(self.n, self.n // self.nt, rt, self.rc)
             self.launches += 1
+            rc = self.rc
         target = self.uc if self.L else self.u
         if self.mode == "learned":
-            self.net.predict(self.nt, self.rc, self.scale, target)
+            self.net.predict(self.nt, rc, self.scale, target)
             self._up(add=False)
             self.hom.set_displacement(self.u)
         elif self.have_prev:                             # delta: u_prev + P(rc) - P(rc_prev)
             if self.L:
-                self.net.predict(self.nt, self.rc, self.scale, self.uc)
+                self.net.predict(self.nt, rc, self.scale, self.uc)
                 self.net.predict(self.nt, self.rc_prev, -self.scale, self.uc, accumulate=True)
                 self.hom.get_displacement(self.u)
                 self._up(add=True)
             else:
                 self.hom.get_displacement(self.u)
-                self.net.predict(self.nt, self.rc, self.scale, self.u, accumulate=True)
+                self.net.predict(self.nt, rc, self.scale, self.u, accumulate=True)
                 self.net.predict(self.nt, self.rc_prev, -self.scale, self.u, accumulate=True)
             self.hom.set_displacement(self.u)
         if self.mode == "delta":
-            self.rc_prev.copy_(self.rc)
+            self.rc_prev.copy_(rc)                        # device-to-device copy of n_t^3 floats
             self.have_prev = True
 
 
