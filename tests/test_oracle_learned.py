@@ -176,3 +176,11 @@ def test_pool_by_brute_force():
                 want = np.mean([g[f * k + c, f * j + b, f * i + a]
                                 for a in range(f) for b in range(f) for c in range(f)])
                 assert abs(got[i + 2 * (j + 2 * k)] - want) < 1e-15
+
+
+def test_features_hand_values():
+    x = L.features(np.array([0.0, 1.0, 0.5, 0.2]), 16)
+    assert x.shape == (4, 16) and np.all(x[:, 3:] == 0)
+    assert np.array_equal(x[0, :3], [0.0, 0.0, 0.0]) and np.array_equal(x[1, :3], [1.0, 1.0, 1.0])
+    assert np.array_equal(x[2, :3], [0.5, 0.25, 0.125])
+    assert np.allclose(x[3, :3], [0.2, 0.04, 0.008], rtol=1e-15, atol=0)
