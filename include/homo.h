@@ -471,7 +471,10 @@ int homo_nn_adam(size_t count, float* w, const float* g, float* m, float* v, int
 int homo_nn_pack(int c_in, const float* w, void* w_fwd, void* w_bwd, void* stream);
 
 /* The network as one object: FP32 master parameters, Adam moments, packed BF16 weights
- * and activation buffers sized on first use for each grid size. */
+ * and activation buffers sized on first use for each grid size. Its calls return
+ * HOMO_OK, HOMO_EINVAL, HOMO_ENOMEM or HOMO_ECUDA, with a message in
+ * homo_net_last_error; they run on the stream of homo_net_set_stream (default: the
+ * legacy default stream). A network is not thread-safe. */
 typedef struct homo_net homo_net;
 
 /* Number of FP32 parameters of a network with `blocks` residual blocks (1..16). */
