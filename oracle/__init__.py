@@ -24,6 +24,9 @@ The oracle is the plain definition of what the method computes, written from the
                derivatives, forward and backward passes with BF16 rounding points,
                MSE loss and Adam (not part of the paper's method; its readings are in
                the module header).
+* pcg.py     - FP64 conjugate gradients preconditioned by block Jacobi or by a symmetric
+               V-cycle of mg.py's operators, certified by the true residual of the
+               assembled K (the solve of Eq. 5 above the sizes a direct solve reaches).
 * mg.py      - explicit trilinear prolongation, Galerkin coarse operators R K I and their
                27-block vertex stencils (Sec. 3.3, Eq. 17-18), 8-colour block Gauss-Seidel
                (Eq. 15-16).

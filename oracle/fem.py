@@ -142,14 +142,21 @@ def macro_strain_loads(n: int, Ee: np.ndarray, Ke: np.ndarray, chi: np.ndarray) 
     return f
 
 
-def solve_cases(K: sp.csr_matrix, f: np.ndarray, method: str = "lu") -> np.ndarray:
+def solve_cases(K: sp.csr_matrix, f: np.ndarray, method: str = "lu", tol: float = 1e-11) -> np.ndarray:
     """Solve K u^i = f^i for every row of f with vertex 0 held at zero (Eq. 5).
 
     K is singular on rigid translations; fixing the three DOFs of vertex 0 (the one
     periodic image of the 8 corner vertices, Sec. 4.2 "Singular stiffness matrices")
-    makes the remaining system SPD. method: "lu" (sparse direct) or "dense" (Cholesky).
+    makes the remaining system SPD. method: "lu" (sparse direct), "dense" (Cholesky), or
+    the FP64 preconditioned CG of pcg.py certified by its true residual ("mgcg": V-cycle
+    preconditioner, "jacobicg": block-Jacobi), returned in the same gauge.
     """
     M = K.shape[0]
+    if method in ("mgcg", "jacobicg"):
+        from .pcg import pcg_solve
+        n = int(round((M // 3) ** (1.0 / 3.0)))
+        assert 3 * n ** 3 == M
+        return pcg_solve(K, f, n, "mg" if method == "mgcg" else "jacobi", tol)
     free = np.arange(3, M)
     Kff = K[free][:, free]
     u = np.zeros_like(f, dtype=np.float64)

@@ -147,6 +147,64 @@ def test_dense_cholesky_and_sparse_lu_agree():
     assert np.allclose(r1["C"], r2["C"], rtol=1e-11, atol=1e-14)
 
 
+@pytest.mark.parametrize("n,kind", [(8, "c1"), (8, "uniform"), (16, "c1"), (16, "uniform")])
+def test_certified_cg_matches_direct_solves(n, kind):
+    """The iterative oracle solves (multigrid- and block-Jacobi-preconditioned CG, certified
+    by the true residual) against sparse LU: displacements in the same gauge, C^H and the
+    bulk sensitivities. The blurred-noise cell has a 5e8 stiffness contrast."""
+    from oracle.pcg import pcg_solve
+    rho = smoothed_threshold_density(n, 0.3, 1) if kind == "c1" else uniform_density(n, 700 + n, 0.05, 1.0)
+    rho_t = oracle.cone_filter(rho.astype(np.float64), n, 2.0)
+    h = 1.0 / n
+    Ke, chi = oracle.ke_hex8(1.0, 0.3, h), oracle.macro_strain_displacements(h)
+    E = oracle.simp_modulus(rho_t)
+    K = oracle.assemble_K(n, E, Ke)
+    f = oracle.macro_strain_loads(n, E, Ke, chi)
+    u_lu = oracle.solve_cases(K, f, "lu")
+    q_lu = oracle.element_energies(n, u_lu, Ke, chi)
+    C_lu = oracle.homogenized_tensor(E, q_lu)
+    _, g = oracle.objective("bulk", C_lu)
+    s_lu = oracle.sensitivity(rho_t, q_lu, g)
+    methods = ["mgcg"] + (["jacobicg"] if (n == 8 or kind == "uniform") else [])
+    for method in methods:
+        info = {}
+        u = pcg_solve(K, f, n, "mg" if method == "mgcg" else "jacobi", 1e-11, info=info)
+        assert info["relres"].max() <= 1e-11
+        assert np.abs(u[:, :3]).max() == 0.0                       # gauge: vertex 0 at zero
+        q = oracle.element_energies(n, u, Ke, chi)
+        C = oracle.homogenized_tensor(E, q)
+        assert np.linalg.norm(C - C_lu) <= 1e-11 * np.linalg.norm(C_lu), method
+        s = oracle.sensitivity(rho_t, q, g)
+        assert np.linalg.norm(s - s_lu) <= 1e-9 * np.linalg.norm(s_lu), method
+        # displacements in the energy norm of each case (void modes are weakly determined)
+        for i in range(6):
+            e = u[i] - u_lu[i]
+            assert e @ (K @ e) <= 1e-18 + 1e-12 * C_lu[i, i], (method, i)
+
+
+def test_certified_cg_full_solid_and_laminate():
+    """Closed forms through the iterative oracle: the full solid returns D with u = 0, and a
+    1-D laminate returns the Backus tensor, at 24^3 where the direct solve is slow."""
+    from oracle.pcg import pcg_solve
+    n = 24
+    h = 1.0 / n
+    Ke, chi = oracle.ke_hex8(1.0, 0.3, h), oracle.macro_strain_displacements(h)
+    E = np.ones(n ** 3)
+    K = oracle.assemble_K(n, E, Ke)
+    u = pcg_solve(K, oracle.macro_strain_loads(n, E, Ke, chi), n)   # loads are rounding residue
+    assert np.abs(u).max() < 1e-12
+    vals = np.array([1.0, 0.1, 0.5, 0.1]) ** (1 / 3)
+    rho = laminate_density(n, 1, vals).astype(np.float64)
+    E = oracle.simp_modulus(rho, Emin=0.0)
+    K = oracle.assemble_K(n, E, Ke)
+    f = oracle.macro_strain_loads(n, E, Ke, chi)
+    u = pcg_solve(K, f, n)
+    C = oracle.homogenized_tensor(E, oracle.element_energies(n, u, Ke, chi))
+    P = _axis_perm_voigt(1)
+    want = _backus(E.reshape(n, n, n)[0, :, 0], 0.3)[np.ix_(P, P)]
+    assert np.abs(C - want).max() < 1e-10
+
+
 def test_solution_satisfies_equilibrium():
     n = 6
     r = oracle.homogenize(uniform_density(n, 22), n)
@@ -372,6 +430,67 @@ def test_objectives_on_isotropic_tensor_and_gradients():
             Cm[i, j] -= 1e-6
             fd = (oracle.objective(kind, Cp, 3)[0] - oracle.objective(kind, Cm, 3)[0]) / 2e-6
             assert abs(fd - g[i, j]) < 1e-7
+
+
+@pytest.mark.parametrize("l", [0, 1, 3])
+def test_relaxed_poisson_objective_hand_values(l):
+    """Eq. 21 on the isotropic D(E=1, nu=0.3): C01+C02+C12 = 3 lambda and
+    C00+C11+C22 = 3 (lambda + 2 mu), so f = 3 lambda - beta^l 3 (lambda + 2 mu); the
+    gradient is +1 on the three named off-diagonal entries and -beta^l on the diagonal."""
+    lam, mu = _lame(1.0, 0.3)
+    assert abs(3 * lam - 0.9 / 0.52) < 1e-15 and abs(3 * (lam + 2 * mu) - 2.1 / 0.52) < 1e-15
+    D = oracle.elasticity_matrix(1.0, 0.3)
+    for beta in (0.8, 0.5):
+        f, g = oracle.objective("poisson", D, iteration=l, beta=beta)
+        want = 0.9 / 0.52 - beta ** l * 3 * 0.7 / 0.52          # 3 lambda - beta^l 3 (lambda + 2 mu)
+        assert abs(f - want) < 1e-14, (f, want)
+        G = np.zeros((6, 6))
+        G[0, 1] = G[0, 2] = G[1, 2] = 1.0
+        G[0, 0] = G[1, 1] = G[2, 2] = -beta ** l
+        assert np.array_equal(g, G)
+    # l = 0: the two sums meet, f = -6 mu
+    assert abs(oracle.objective("poisson", D, iteration=0)[0] + 6 * mu) < 1e-14
+
+
+def test_log_poisson_objective_hand_values():
+    """Eq. 22 with eta = 0.6, tau = -1/E0^gamma, gamma = 0.5. On the isotropic D the
+    ratio (C01+C12+C20)/(C00+C11+C22) is nu/(1-nu) = 3/7 and the trace is 3 (1-nu)/
+    ((1+nu)(1-2nu)) = 2.1/0.52, so f = log(1 + 0.6*3/7) - sqrt(2.1/0.52)."""
+    D = oracle.elasticity_matrix(1.0, 0.3)
+    f, g = oracle.objective("logpoisson", D)
+    want = np.log(1.0 + 0.6 * 3.0 / 7.0) - np.sqrt(2.1 / 0.52)
+    assert abs(f - want) < 1e-14, (f, want)
+    # E0 = 4: tau = -1/2, the second term halves
+    f4, _ = oracle.objective("logpoisson", D, E0=4.0)
+    assert abs(f4 - (np.log(1.0 + 0.6 * 3.0 / 7.0) - 0.5 * np.sqrt(2.1 / 0.52))) < 1e-14
+    # hand gradient: a = 3 lambda, b = 3 (lambda + 2 mu); df/da = eta / (b + eta a),
+    # df/db = -eta a / (b (b + eta a)) - gamma b^(gamma - 1)
+    a, b = 0.9 / 0.52, 2.1 / 0.52
+    da = 0.6 / (b + 0.6 * a)
+    db = -0.6 * a / (b * (b + 0.6 * a)) - 0.5 / np.sqrt(b)
+    for (i, j) in ((0, 1), (1, 2), (2, 0)):
+        assert abs(g[i, j] - da) < 1e-15
+    for i in range(3):
+        assert abs(g[i, i] - db) < 1e-15
+    assert g[1, 0] == g[2, 1] == g[0, 2] == 0.0 and np.all(g[3:, :] == 0) and np.all(g[:, 3:] == 0)
+
+
+def test_poisson_objectives_on_a_worked_anisotropic_tensor():
+    """A non-symmetric C whose entries name their index set: C02 = 0.25 but C20 = 0.75.
+    Eq. 21 reads C01, C02, C12; Eq. 22 reads C01, C12, C20.
+      Eq. 21, beta = 0.8, l = 1: 0.5 + 0.25 + 1 - 0.8 (2 + 3 + 5) = -6.25
+      Eq. 22: a = 0.5 + 1 + 0.75 = 2.25, b = 10: log(1 + 0.6 * 0.225) - sqrt(10)
+      bulk (Eq. 19): -(10 + 2 (0.5 + 0.25 + 1)) / 9 = -13.5 / 9
+      shear (Eq. 20): -(0.4 + 0.7 + 0.9) / 3"""
+    C = np.zeros((6, 6))
+    C[0, 0], C[1, 1], C[2, 2] = 2.0, 3.0, 5.0
+    C[0, 1], C[0, 2], C[1, 2] = 0.5, 0.25, 1.0
+    C[1, 0], C[2, 0], C[2, 1] = 0.5, 0.75, 1.0
+    C[3, 3], C[4, 4], C[5, 5] = 0.4, 0.7, 0.9
+    assert abs(oracle.objective("poisson", C, iteration=1, beta=0.8)[0] + 6.25) < 1e-14
+    assert abs(oracle.objective("logpoisson", C)[0] - (np.log(1.135) - np.sqrt(10.0))) < 1e-14
+    assert abs(oracle.objective("bulk", C)[0] + 13.5 / 9.0) < 1e-15
+    assert abs(oracle.objective("shear", C)[0] + 2.0 / 3.0) < 1e-15
 
 
 def test_paper_parameters_golden():
