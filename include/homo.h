@@ -239,6 +239,20 @@ int homo_solve_batch(homo_ctx* const* ctxs, int count, double rel_tol, int max_i
 #define HOMO_RESIDUAL_DOUBLE_FLOAT 1
 int homo_residual(homo_ctx* ctx, int method, double relres_out[6]);
 
+/* Residual fields, for parity tests of the finest-level residual kernels (the residual
+ * of Eq. 5 evaluated in the vertex form of Eq. 13). out: device, 18 planes of n^3 floats
+ * (plane = 3 case + component, x fastest), written by the call; nothing is removed from
+ * it (rigid translations included).
+ *   method HOMO_RESIDUAL_FP32 or HOMO_RESIDUAL_DOUBLE_FLOAT: the context's true residual
+ *     f - K (u_hi + u_lo) of its own loads and displacement (the evaluations of
+ *     homo_residual); b and u must be NULL.
+ *   method HOMO_RESIDUAL_VCYCLE: b - K u for caller fields b and u (device, 18 n^3 floats
+ *     each, neither aliasing out), the evaluation the V-cycle uses on the finest level.
+ * Returns HOMO_ESTATE before homo_set_density, HOMO_EINVAL on a bad method or pointer
+ * combination. Synchronises the stream. */
+#define HOMO_RESIDUAL_VCYCLE 2
+int homo_residual_field(homo_ctx* ctx, int method, const float* b, const float* u, float* out);
+
 /* C^H without any device allocation (the paper has no counterpart to this entry point).
  * For callers that cannot call cudaMalloc while they run: an application that sets its
  * device-memory budget once at start-up, a framework whose own pooled allocator must
@@ -310,6 +324,15 @@ int homo_element_jacobi_bound(double nu, double* out);
 int homo_get_displacement(homo_ctx* ctx, float* u);
 int homo_set_displacement(homo_ctx* ctx, const float* u);
 
+/* Exact copy of the displacement state that warm-starts the next solve: both FP32 parts
+ * of the double-float fields u = hi + lo (18*N floats each, device, caller-owned).
+ * Restoring a saved state makes the next warm-started solve repeat the one that followed
+ * the save, iteration for iteration. Neither pointer may be NULL; enqueued on the
+ * context's stream (no synchronisation). The paper has no counterpart (it keeps the
+ * previous iterate in place, Sec. 4.1). */
+int homo_save_displacement(homo_ctx* ctx, float* hi, float* lo);
+int homo_restore_displacement(homo_ctx* ctx, const float* hi, const float* lo);
+
 /* Assembled macro-strain loads f_i = sum_e E_e K0 chi_i,e for the current density
  * (Eq. 4 in the vertex form Eq. 11, element-relative chi of Eq. 12). f: 18*N floats. */
 int homo_get_loads(homo_ctx* ctx, float* f);
@@ -358,7 +381,7 @@ int homo_vcycle(homo_ctx* ctx, const float* r, float* z);
 
 /* Kernel classes for per-class device timing. */
 #define HOMO_KC_FINE_MATVEC 0      /* CG product q = K p on the finest level (Eq. 13)      */
-#define HOMO_KC_FINE_RESIDUAL 1    /* finest-level residuals (V-cycle and true residual)   */
+#define HOMO_KC_FINE_RESIDUAL 1    /* finest-level V-cycle residuals b - K u               */
 #define HOMO_KC_FINE_GS 2          /* finest-level Gauss-Seidel colour passes (Eq. 15-16)  */
 #define HOMO_KC_COARSE_GS 3        /* coarse-level Gauss-Seidel colour passes              */
 #define HOMO_KC_COARSE_RESIDUAL 4  /* coarse-level residuals                               */
@@ -372,7 +395,8 @@ int homo_vcycle(homo_ctx* ctx, const float* r, float* z);
 #define HOMO_KC_OTHER 12           /* SIMP moduli, field copies, stencil export             */
 #define HOMO_KC_FINE_CHEB 13       /* finest-level Chebyshev smoothing steps                */
 #define HOMO_KC_COARSE_CHEB 14     /* coarse-level Chebyshev smoothing steps                */
-#define HOMO_KC_COUNT 15
+#define HOMO_KC_TRUE_RESIDUAL 15   /* true residuals f - K u (FP32 and double-float forms) */
+#define HOMO_KC_COUNT 16
 
 /* Start (enable = 1, counters reset) or stop (0) recording a CUDA event pair around
  * every kernel launch of the context, on its stream. */
@@ -384,6 +408,15 @@ int homo_profile_read(homo_ctx* ctx, int kc, long long* launches, double* total_
 
 /* Static name of a kernel class ("fine_matvec", ...), or "" for an unknown class. */
 const char* homo_kernel_class_name(int kc);
+
+/* Measured FP32 arithmetic peak of the current device, the denominator of the roofline of
+ * the ALU-bound stencil kernels (the paper reports no such figure). A kernel of independent
+ * FMA chains fills every SM (8 chains per thread, 1024 threads per SM); its CUDA-event
+ * time gives TFLOP/s = 2 flops per FMA lane. packed = 0: scalar fma.rn.f32; packed = 1:
+ * the two-lane fma.rn.f32x2 of sm_100 and later (4 flops per instruction).
+ *   tflops_out: host, 1 double (output).
+ * Allocates and frees a small device buffer; synchronises the device's legacy stream. */
+int homo_probe_fp32_peak(int packed, double* tflops_out);
 
 /* Total number of kernels this context has launched since it was created. */
 long long homo_launch_count(const homo_ctx* ctx);

@@ -65,6 +65,10 @@ SIGNATURES = {
     "homo_set_displacement": (ctypes.c_int, [_vp, _vp]),
     "homo_get_loads": (ctypes.c_int, [_vp, _vp]),
     "homo_apply_K": (ctypes.c_int, [_vp, _vp, _vp]),
+    "homo_residual_field": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _vp]),
+    "homo_save_displacement": (ctypes.c_int, [_vp, _vp, _vp]),
+    "homo_restore_displacement": (ctypes.c_int, [_vp, _vp, _vp]),
+    "homo_probe_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "homo_get_stencil": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "homo_restrict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "homo_prolong": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -111,7 +115,7 @@ NN_CHANNELS, NN_FEATURES = 32, 16
 NN_EPILOGUES = {"relu": 0, "mask": 1, "planes": 2, "planes_add": 3}
 NN_MSE_SCRATCH = 1025
 
-KERNEL_CLASSES = 15
+KERNEL_CLASSES = 16
 
 _lib = None
 
@@ -172,6 +176,16 @@ def solve_batch(homs, rel_tol: float, max_iters: int = 500, warm_start: bool = T
         raise HomoError(rc, lib.homo_last_error(homs[bad].h).decode())
     return (np.array(its[:], dtype=np.int64).reshape(count, 6), np.array(rel[:]).reshape(count, 6),
             list(st[:]))
+
+
+def probe_fp32_peak(packed: bool = False) -> float:
+    """Measured FP32 FMA throughput of the current device in TFLOP/s (scalar or f32x2)."""
+    lib = load_library()
+    out = ctypes.c_double()
+    st = lib.homo_probe_fp32_peak(1 if packed else 0, ctypes.byref(out))
+    if st != 0:
+        raise HomoError(st, "homo_probe_fp32_peak failed")
+    return out.value
 
 
 def objective(kind: str, CH, iteration: int = 0, param: float = 0.8):
@@ -294,6 +308,13 @@ class Homogenization:
     def set_displacement(self, u):
         self._check(self.lib.homo_set_displacement(self.h, _vp(_ptr(u))))
 
+    def save_displacement(self, hi, lo):
+        """Both parts of the double-float displacement into hi, lo (18 n^3 floats each)."""
+        self._check(self.lib.homo_save_displacement(self.h, _vp(_ptr(hi)), _vp(_ptr(lo))))
+
+    def restore_displacement(self, hi, lo):
+        self._check(self.lib.homo_restore_displacement(self.h, _vp(_ptr(hi)), _vp(_ptr(lo))))
+
     def get_loads(self, out):
         self._check(self.lib.homo_get_loads(self.h, _vp(_ptr(out))))
 
@@ -357,6 +378,14 @@ class Homogenization:
         out = (ctypes.c_double * 6)()
         self._check(self.lib.homo_residual(self.h, m, out))
         return np.array(out[:])
+
+    def residual_field(self, method: str, out, b=None, u=None):
+        """Residual field into out (18 n^3 floats): "fp32" / "double_float" = the context's
+        f - K (u_hi + u_lo); "vcycle" = b - K u for the given fields."""
+        m = {"fp32": 0, "double_float": 1, "vcycle": 2}[method]
+        bp = None if b is None else _vp(_ptr(b))
+        up = None if u is None else _vp(_ptr(u))
+        self._check(self.lib.homo_residual_field(self.h, m, bp, up, _vp(_ptr(out))))
 
     def residual_history(self) -> np.ndarray:
         """(records, 6) relative residuals of the last solve."""

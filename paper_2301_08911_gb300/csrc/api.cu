@@ -373,9 +373,9 @@ int enq_read(homo_ctx* c, int slot, int count) {
 int enq_true_residual(homo_ctx* c, double tol, bool exact) {
   int g = 0;
   if (exact)
-    KL(c, HOMO_KC_FINE_RESIDUAL, 1, launch_fine_residual(c, c->f, c->u, c->ulo, c->r, c->part, &g, nullptr));
+    KL(c, HOMO_KC_TRUE_RESIDUAL, 1, launch_fine_residual(c, c->f, c->u, c->ulo, c->r, c->part, &g, nullptr));
   else
-    KL(c, HOMO_KC_FINE_RESIDUAL, 1,
+    KL(c, HOMO_KC_TRUE_RESIDUAL, 1,
        launch_fine_tiled(c, 2, c->u, c->f, c->r, c->part, &g, nullptr, 0.f, 0.f, c->ulo));
   KL(c, HOMO_KC_CG_VECTOR, 1, launch_sum_partials(c->part, g, kCases + kPlanes, c->scal + S_RR, c->stream));
   KL(c, HOMO_KC_CG_VECTOR, 1, launch_cg_active(c->scal, tol, c->N, c->stream));
@@ -1038,6 +1038,26 @@ int homo_residual(homo_ctx* ctx, int method, double relres_out[6]) {
   return HOMO_OK;
 }
 
+int homo_residual_field(homo_ctx* ctx, int method, const float* b, const float* u, float* out) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!out) return set_err(ctx, HOMO_EINVAL, "residual_field: NULL output");
+  if (method == HOMO_RESIDUAL_VCYCLE) {
+    if (!b || !u || b == out || u == out) return set_err(ctx, HOMO_EINVAL, "residual_field: bad b/u/out");
+    if (!ctx->density_set) return set_err(ctx, HOMO_ESTATE, "no density set");
+    KL(ctx, HOMO_KC_FINE_RESIDUAL, 1, launch_fine_residual(ctx, b, u, nullptr, out, nullptr, nullptr, nullptr));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    prof_flush(ctx);
+    return HOMO_OK;
+  }
+  if ((method != HOMO_RESIDUAL_FP32 && method != HOMO_RESIDUAL_DOUBLE_FLOAT) || b || u)
+    return set_err(ctx, HOMO_EINVAL, "residual_field: bad method or b/u given");
+  RET(ensure_loads(ctx));
+  RET(true_residual(ctx, 1.0, method == HOMO_RESIDUAL_DOUBLE_FLOAT));
+  CK(ctx, cudaMemcpyAsync(out, ctx->r, sizeof(float) * kPlanes * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(ctx, cudaStreamSynchronize(ctx->stream));
+  return HOMO_OK;
+}
+
 int homo_CH(homo_ctx* ctx, double CH[36]) {
   if (!ctx || !CH) return HOMO_EINVAL;
   if (!ctx->solved) return set_err(ctx, HOMO_ESTATE, "homo_CH needs a solve first");
@@ -1125,6 +1145,23 @@ int homo_get_displacement(homo_ctx* ctx, float* u) {
 int homo_set_displacement(homo_ctx* ctx, const float* u) {
   if (!ctx || !u) return HOMO_EINVAL;
   KL(ctx, HOMO_KC_OTHER, 1, launch_split_set(ctx->u, ctx->ulo, u, kPlanes * ctx->N, ctx->stream));
+  ctx->solved = false;
+  return HOMO_OK;
+}
+
+int homo_save_displacement(homo_ctx* ctx, float* hi, float* lo) {
+  if (!ctx || !hi || !lo) return HOMO_EINVAL;
+  const size_t bytes = sizeof(float) * kPlanes * ctx->N;
+  CK(ctx, cudaMemcpyAsync(hi, ctx->u, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(ctx, cudaMemcpyAsync(lo, ctx->ulo, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  return HOMO_OK;
+}
+
+int homo_restore_displacement(homo_ctx* ctx, const float* hi, const float* lo) {
+  if (!ctx || !hi || !lo) return HOMO_EINVAL;
+  const size_t bytes = sizeof(float) * kPlanes * ctx->N;
+  CK(ctx, cudaMemcpyAsync(ctx->u, hi, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+  CK(ctx, cudaMemcpyAsync(ctx->ulo, lo, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
   ctx->solved = false;
   return HOMO_OK;
 }
@@ -1292,7 +1329,7 @@ int homo_profile_read(homo_ctx* ctx, int kc, long long* launches, double* total_
 const char* homo_kernel_class_name(int kc) {
   static const char* names[HOMO_KC_COUNT] = {
       "fine_matvec", "fine_residual", "fine_gs", "coarse_gs", "coarse_residual", "transfer", "coarsest",
-      "setup", "cg_vector", "element", "filter", "oc", "other", "fine_cheb", "coarse_cheb"};
+      "setup", "cg_vector", "element", "filter", "oc", "other", "fine_cheb", "coarse_cheb", "true_residual"};
   return (kc >= 0 && kc < HOMO_KC_COUNT) ? names[kc] : "";
 }
 

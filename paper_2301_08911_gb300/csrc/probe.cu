@@ -1,0 +1,88 @@
+// Measured FP32 FMA peak of the device: the denominator of the ALU roofline of the
+// finest-level stencil kernels, which run on the CUDA cores.
+#include <cuda_runtime.h>
+
+#include "homo.h"
+
+namespace {
+
+constexpr int kChains = 8;        // independent FMA chains per thread: hides the FMA latency
+constexpr int kThreads = 256;
+constexpr int kBlocksPerSm = 4;   // 1024 threads per SM
+constexpr int kIters = 4096;
+
+__global__ void __launch_bounds__(kThreads) k_fma_scalar(float* out, float a, float b) {
+  float acc[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) acc[c] = static_cast<float>(threadIdx.x + c);
+  for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) acc[c] = fmaf(acc[c], a, b);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += acc[c];
+  out[blockIdx.x * kThreads + threadIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads) k_fma_packed(float* out, float a, float b) {
+  unsigned long long acc[kChains], ma, mb;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(ma) : "f"(a));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(mb) : "f"(b));
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    const float x = static_cast<float>(threadIdx.x + c), y = x + 0.5f;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(acc[c]) : "f"(x), "f"(y));
+  }
+  for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(acc[c]) : "l"(ma), "l"(mb));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[c]));
+    s += lo + hi;
+  }
+  out[blockIdx.x * kThreads + threadIdx.x] = s;
+}
+
+}  // namespace
+
+extern "C" int homo_probe_fp32_peak(int packed, double* tflops_out) {
+  if (!tflops_out || (packed != 0 && packed != 1)) return HOMO_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HOMO_ECUDA;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return HOMO_ECUDA;
+  const int blocks = sms * kBlocksPerSm;
+  float* out = nullptr;
+  if (cudaMalloc(&out, sizeof(float) * blocks * kThreads) != cudaSuccess) return HOMO_ENOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = HOMO_OK;
+  float best = 0.f;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = HOMO_ECUDA;
+  // a = 1 - 2^-20 and b = 2^-10 keep every chain finite and away from denormals
+  const float a = 0.99999905f, b = 0.0009765625f;
+  for (int rep = 0; rep < 4 && st == HOMO_OK; ++rep) {      // first launch warms clocks up
+    cudaEventRecord(e0, 0);
+    if (packed) k_fma_packed<<<blocks, kThreads>>>(out, a, b);
+    else k_fma_scalar<<<blocks, kThreads>>>(out, a, b);
+    cudaEventRecord(e1, 0);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      st = HOMO_ECUDA;
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(out);
+  if (st != HOMO_OK) return st;
+  const double lanes = packed ? 2.0 : 1.0;
+  const double flops = 2.0 * lanes * kChains * static_cast<double>(kIters) * blocks * kThreads;
+  *tflops_out = flops / (best * 1e-3) / 1e12;
+  return HOMO_OK;
+}
