@@ -35,10 +35,27 @@ __global__ void __launch_bounds__(BLOCK, (CASES == 3 ? 1024 : 512) / BLOCK)
     const Nb nb = make_nb(x, y, z, n);
     float Et[8];
     load_E8(E, nb, Et);
-    float rhs[3 * kGsCases];
+    // The cases advance in pairs (c, c + 1) on the two lanes of f32x2 registers: pair
+    // p holds cases 2p and 2p + 1, a lone last case (CASES = 3) runs in scalar FMAs.
+    constexpr int kPairs = kGsCases / 2;
+    constexpr bool kOdd = (kGsCases & 1) != 0;
+    f32x2 rp[3 * kPairs];
+    float rs[3];
 #pragma unroll
-    for (int q = 0; q < 3 * kGsCases; ++q)
-      rhs[q] = __ldg(f + (q0 + q) * N + v) - (fmean ? static_cast<float>(fmean[q0 + q]) : 0.f);
+    for (int p = 0; p < kPairs; ++p)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int qa = 3 * (2 * p) + r, qb = qa + 3;
+        rp[3 * p + r] = pack2(__ldg(f + (q0 + qa) * N + v) - (fmean ? static_cast<float>(fmean[q0 + qa]) : 0.f),
+                              __ldg(f + (q0 + qb) * N + v) - (fmean ? static_cast<float>(fmean[q0 + qb]) : 0.f));
+      }
+    if (kOdd) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const int q = 3 * (kGsCases - 1) + r;
+        rs[r] = __ldg(f + (q0 + q) * N + v) - (fmean ? static_cast<float>(fmean[q0 + q]) : 0.f);
+      }
+    }
 #pragma unroll
     for (int d = 0; d < 27; ++d) {
       if (d == 13) continue;
@@ -47,16 +64,37 @@ __global__ void __launch_bounds__(BLOCK, (CASES == 3 ? 1024 : 512) / BLOCK)
       if (first && (colour ^ odd) > colour) continue;
       float A[9];
       nb_block(K, Et, dx, dy, dz, A);
+      f32x2 nA[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) nA[e] = pack2(-A[e], -A[e]);
       const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
       const float* ur = u + q0 * N + w;
 #pragma unroll
-      for (int c = 0; c < kGsCases; ++c) {
+      for (int p = 0; p < kPairs; ++p) {
+        f32x2 uu[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) uu[k] = pack2(__ldg(ur + (6 * p + k) * N), __ldg(ur + (6 * p + 3 + k) * N));
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          rp[3 * p + r] = ffma2(nA[3 * r + 2], uu[2], ffma2(nA[3 * r + 1], uu[1], ffma2(nA[3 * r], uu[0], rp[3 * p + r])));
+      }
+      if (kOdd) {
+        const int c = kGsCases - 1;
         const float u0 = __ldg(ur + (3 * c) * N), u1 = __ldg(ur + (3 * c + 1) * N),
                     u2 = __ldg(ur + (3 * c + 2) * N);
 #pragma unroll
         for (int r = 0; r < 3; ++r)
-          rhs[3 * c + r] = fmaf(-A[3 * r + 2], u2, fmaf(-A[3 * r + 1], u1, fmaf(-A[3 * r], u0, rhs[3 * c + r])));
+          rs[r] = fmaf(-A[3 * r + 2], u2, fmaf(-A[3 * r + 1], u1, fmaf(-A[3 * r], u0, rs[r])));
       }
+    }
+    float rhs[3 * kGsCases];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) unpack2(rp[3 * p + r], rhs[3 * (2 * p) + r], rhs[3 * (2 * p + 1) + r]);
+    if (kOdd) {
+#pragma unroll
+      for (int r = 0; r < 3; ++r) rhs[3 * (kGsCases - 1) + r] = rs[r];
     }
     float S[9];
     nb_block(K, Et, 0, 0, 0, S);

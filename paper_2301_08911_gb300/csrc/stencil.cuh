@@ -50,6 +50,40 @@ __device__ __forceinline__ void nb_block(const KeParam& K, const float (&Et)[8],
   A[6] = C[48] * s02;     A[7] = C[49] * s12;     A[8] = C[50] * s0;
 }
 
+// Two FP32 lanes in one 64-bit register pair, for the two-lane FMA of sm_100 and later
+// (fma.rn.f32x2): each lane is rounded exactly like a scalar fmaf, so a pair of load
+// cases advanced together gives bitwise the result of two scalar chains in the same order.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+
+__device__ __forceinline__ void unpack2(f32x2 p, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+
+// d = a * b + c per lane
+__device__ __forceinline__ f32x2 ffma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+__device__ __forceinline__ f32x2 fsub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+__device__ __forceinline__ f32x2 fadd2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // Solve the SPD 3x3 system S y = b for NC right-hand sides (LDL^T, FP32).
 template <int NC>
 __device__ __forceinline__ void solve3xn(const float (&S)[9], float (&b)[3 * NC]) {
