@@ -31,8 +31,6 @@ if ROOT not in sys.path:
 
 PAPER_512_BULK_MS = 38030.0      # paper, 512^3 bulk vf 0.3: 38.03 s per iteration (GTX 1080Ti)
 METRIC = "ms per opt. iteration at 256\u00b3/512\u00b3 (6 cases to rel-res 1e-5); stencil HBM GB/s"
-FP32_LANES_PER_SM = 128
-NUM_SMS = 152
 
 
 def parse_args(argv=None):
@@ -47,7 +45,11 @@ def parse_args(argv=None):
     ap.add_argument("--tol", type=float, default=1e-5)
     ap.add_argument("--max-iters", type=int, default=1000)
     ap.add_argument("--seed", type=int, default=5)
-    ap.add_argument("--sample-n", type=int, default=16, help="cell size of the oracle's CPU sample")
+    ap.add_argument("--sample-n", type=int, default=16, help="cell size of the reference arm's oracle sample")
+    ap.add_argument("--second-n", type=int, default=256,
+                    help="also time this cell size (5 steps after 3 warm-up); 0 = off")
+    ap.add_argument("--profile-steps", type=int, default=5,
+                    help="steps of the separate per-launch-timed replay that gives the kernel breakdown")
     ap.add_argument("--sweeps", type=int, default=0,
                     help="smoothing sweeps before/after coarse correction (0 = library default, 1)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
@@ -208,8 +210,10 @@ def algorithmic_work(kc: str, n: int, sweeps: int = 1):
         return b, f
     if kc == "fine_matvec":      # E 4N + p 72N + q 72N; difference form: 26 blocks + 468 sub
         return 148 * N, ((576 + 26 * 54) * 2 + 26 * 18) * N
-    if kc == "fine_residual":    # E 4N + x 72N + b 72N + out 72N
+    if kc == "fine_residual":    # V-cycle residual: E 4N + x 72N + b 72N + out 72N
         return 220 * N, STENCIL_FLOP * N
+    if kc == "true_residual":    # f - K (u + ulo): E 4N + u 72N + ulo 72N + f 72N + out 72N
+        return 292 * N, STENCIL_FLOP * N
     if kc == "element":          # u 72N + E/rho 8N (+ out 4N); 6 x 576 + 21 x 24 FMA per element
         return 80 * N, (6 * 576 + 21 * 24) * 2 * N
     return None, None
@@ -244,28 +248,80 @@ sys.path.insert(0, {root!r})
 import numpy as np
 import oracle
 from synthetic import smoothed_threshold_density
-n, vf, kind, reps = {n}, {vf}, {kind!r}, {reps}
+n, vf, kind, reps, method = {n}, {vf}, {kind!r}, {reps}, {method!r}
 rho = smoothed_threshold_density(n, vf, {seed}).astype(np.float64)
 times = []
 for it in range(reps):
     t0 = time.perf_counter()
-    out = oracle.optimization_iteration(rho, n, vf, kind, iteration=it)
+    out = oracle.optimization_iteration(rho, n, vf, kind, iteration=it, method=method, tol=1e-9)
     times.append(time.perf_counter() - t0)
     rho = out["rho_new"]
 print(json.dumps({{"times_s": times}}))
 """
 
+# the oracle's solve at each sample size: sparse LU at 16^3, its certified multigrid-
+# preconditioned FP64 CG above (sparse LU at 32^3 takes tens of minutes)
+ORACLE_METHOD = {16: "lu"}
 
-def oracle_sample(n: int, vf: float, kind: str, reps: int, seed: int):
-    """Time `reps` oracle iterations at n^3 in a fresh single-threaded process."""
+
+def oracle_sample(n: int, vf: float, kind: str, reps: int, seed: int, procs: int = 1):
+    """Time `reps` oracle iterations at n^3 in `procs` concurrent single-threaded processes
+    (seeds seed, seed+1, ...). Returns (per-process lists of seconds, wall seconds)."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
-    code = _ORACLE_SNIPPET.format(root=ROOT, n=n, vf=vf, kind=kind, reps=reps, seed=seed)
-    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if p.returncode != 0:
-        raise RuntimeError(p.stderr[-2000:])
-    return json.loads(p.stdout.strip().splitlines()[-1])["times_s"]
+    method = ORACLE_METHOD.get(n, "mgcg")
+    t0 = time.perf_counter()
+    ps = [subprocess.Popen([sys.executable, "-c", _ORACLE_SNIPPET.format(
+        root=ROOT, n=n, vf=vf, kind=kind, reps=reps, seed=seed + k, method=method)],
+        stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env) for k in range(procs)]
+    outs = []
+    for p in ps:
+        so, se = p.communicate(timeout=1800)
+        if p.returncode != 0:
+            raise RuntimeError(se[-2000:])
+        outs.append(json.loads(so.strip().splitlines()[-1])["times_s"])
+    return outs, time.perf_counter() - t0
+
+
+def host_cpu() -> dict:
+    """Core count and CPU model of the host the oracle runs on."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
+def oracle_baseline(args, n_target: int) -> dict:
+    """The FP64 oracle timed on this host: one thread at 16^3 (2 iterations) and 32^3 (one
+    iteration), and all cores at once at 32^3 (one iteration per core, different seeds).
+    The value in the metric's unit scales the measured 32^3 single-thread time by element
+    count to n_target^3 (a lower bound: the oracle's CG iteration count grows with n); the
+    measured sizes are reported as measured."""
+    host = host_cpu()
+    procs = max(1, min(int(host["nproc"] or 1), 64))
+    t16, _ = oracle_sample(16, args.vf, args.objective, 2, args.seed)
+    t32, _ = oracle_sample(32, args.vf, args.objective, 1, args.seed)
+    tall, wall = oracle_sample(32, args.vf, args.objective, 1, args.seed, procs=procs)
+    ms16 = 1000.0 * statistics.mean(t16[0])
+    ms32 = 1000.0 * statistics.mean(t32[0])
+    return {"value": ms32 * (n_target / 32) ** 3, "unit": "ms", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 oracle (numpy/scipy; sparse LU at 16^3, certified multigrid-preconditioned CG "
+                       f"to true relative residual 1e-9 at 32^3) optimisation iterations measured at 16^3 and 32^3 on this host; "
+                       f"value = the 32^3 single-thread time x (n/32)^3 to {n_target}^3 (lower bound; "
+                       f"256^3 and 512^3 are not run: the oracle's assembled K alone is 49 / 390 GB)"),
+            "measured": {"16^3": {"ms_per_iteration": ms16, "threads": 1, "iterations": len(t16[0])},
+                         "32^3": {"ms_per_iteration": ms32, "threads": 1, "iterations": 1},
+                         "32^3_all_cores": {"ms_per_iteration": 1000.0 * wall / procs, "processes": procs,
+                                            "threads_per_process": 1,
+                                            "note": "throughput: one iteration per process, all at once"}},
+            "host": host}
 
 
 def workload_name(args):
@@ -296,21 +352,28 @@ def config_dict(args):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
+    """The oracle as it stands, timed on the host cores for the same workload: each step is
+    one oracle optimisation iteration of a 32^3 sample of the workload's generator, scaled
+    by element count to the workload's n^3 (a lower bound)."""
     if rank != 0:
         return 0
     reps = args.warmup + args.steps
-    times = oracle_sample(args.sample_n, args.vf, args.objective, reps, args.seed)
-    timed = times[args.warmup:]
-    scale = (args.n ** 3) / (args.sample_n ** 3)
+    sn = args.sample_n
+    outs, _ = oracle_sample(sn, args.vf, args.objective, reps, args.seed)
+    timed = outs[0][args.warmup:]
+    scale = (args.n ** 3) / (sn ** 3)
     ms = 1000.0 * statistics.mean(timed) * scale
-    sample = (f"oracle (numpy/scipy FP64, sparse LU solve) optimisation iterations at "
-              f"{args.sample_n}^3, {args.steps} timed after {args.warmup} warm-up, scaled linearly by "
-              f"element count to {args.n}^3 (a lower bound: the direct solve grows faster than linearly)")
+    method = ORACLE_METHOD.get(sn, "mgcg")
+    sample = (f"FP64 oracle (numpy/scipy, {'sparse LU' if method == 'lu' else 'certified multigrid-preconditioned CG'}) "
+              f"optimisation iterations at {sn}^3 (same generator, vf, objective), {args.steps} timed after "
+              f"{args.warmup} warm-up, one thread, scaled by element count to {args.n}^3 (a lower bound)")
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": "ms",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(args),
-            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": ms, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample,
+                             "measured_ms_per_iteration": {f"{sn}^3": 1000.0 * statistics.mean(timed)},
+                             "host": host_cpu()},
             "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -461,155 +524,252 @@ class LearnedStart:
 
 
 # ------------------------------------------------------------------ our arm
+STENCIL_CLASSES = ("fine_matvec", "fine_residual", "fine_gs", "true_residual")
+
+
+def roofline_of(kc: str, kn: int, kms: float, n: int, sweeps: int, peak_hbm: float, peak_src: str,
+                alu_peak: float, alu_src: str):
+    """Roofline entry of a kernel class from its launch count and summed event time."""
+    nbytes, nflops = algorithmic_work(kc, n, sweeps)
+    if nbytes is None or kn <= 0:
+        return None
+    avg_s = kms / kn / 1000.0
+    t_hbm = nbytes / (peak_hbm * 1e9)
+    t_alu = nflops / (alu_peak * 1e12)
+    gbs = nbytes / avg_s / 1e9
+    tfl = nflops / avg_s / 1e12
+    traffic = recorded_traffic(kc, n)
+    base = {"kernel": kc, "avg_launch_ms": kms / kn, "launches": kn, "bytes_per_launch": nbytes,
+            "flops_per_launch": nflops, "traffic": traffic, "hbm_gbs": gbs, "hbm_frac": gbs / peak_hbm,
+            "alu_tflops": tfl, "alu_frac": tfl / alu_peak}
+    if t_hbm >= t_alu:
+        return dict(bound="hbm", achieved=gbs, peak=peak_hbm, unit="GB/s", frac=gbs / peak_hbm,
+                    peak_source=peak_src, **base)
+    return dict(bound="alu", achieved=tfl, peak=alu_peak, unit="TFLOP/s", frac=tfl / alu_peak,
+                peak_source=alu_src, **base)
+
+
+class Loop:
+    """The optimisation loop of Sec. 5.2 on one cell, with exact snapshots of everything a
+    step carries to the next (density, iteration counter, both parts of the displacement,
+    the learned start's previous pooled density), so passes can replay the same steps."""
+
+    def __init__(self, args, n, seed, stream, dev, warm_start="previous"):
+        import torch
+
+        from paper_2301_08911_gb300 import binding
+        from synthetic import smoothed_threshold_density
+        self.b, self.args, self.n, self.stream, self.dev = binding, args, n, stream, dev
+        self.hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream,
+                                          smoother=args.smoother, precision=args.precision)
+        self.r = torch.from_numpy(smoothed_threshold_density(n, args.vf, seed)).to(dev)
+        self.rt = torch.empty_like(self.r)
+        self.s = torch.empty_like(self.r)
+        self.dc = torch.empty_like(self.r)
+        self.it = 0
+        self.cg, self.relres = [], []
+        self.learned = None
+
+    def step(self):
+        a, hom = self.args, self.hom
+        hom.filter(2.0, self.r, self.rt)
+        hom.set_density(self.rt)
+        if self.learned is not None:
+            self.learned(self.rt)
+        its, rel, _ = hom.solve_cases(a.tol, a.max_iters, warm_start=True, raise_on_noconv=False)
+        C = hom.CH()
+        f, g = self.b.objective(a.objective, C, self.it, 0.8)
+        hom.sensitivity(g, self.s)
+        hom.filter(2.0, self.s, self.dc)
+        if a.sym != "none":
+            hom.symmetrize(a.sym, self.dc, self.dc)
+        hom.update(self.dc, self.r, a.vf)
+        if a.sym != "none":
+            hom.symmetrize(a.sym, self.r, self.r)
+        self.it += 1
+        self.cg.append(its)
+        self.relres.append(max(rel))
+        return f
+
+    def launches(self):
+        lr = self.learned
+        return self.hom.launch_count + (lr.net.launch_count + lr.launches if lr else 0)
+
+    def snapshot(self):
+        import torch
+        N18 = 18 * self.n ** 3
+        snap = {"r": self.r.clone(), "it": self.it, "hi": torch.empty(N18, device=self.dev),
+                "lo": torch.empty(N18, device=self.dev)}
+        self.hom.save_displacement(snap["hi"], snap["lo"])
+        lr = self.learned
+        if lr is not None and lr.rc_prev is not None:
+            snap["rc_prev"], snap["have_prev"] = lr.rc_prev.clone(), lr.have_prev
+        return snap
+
+    def restore(self, snap):
+        self.r.copy_(snap["r"])
+        self.it = snap["it"]
+        self.hom.restore_displacement(snap["hi"], snap["lo"])
+        if "rc_prev" in snap:
+            self.learned.rc_prev.copy_(snap["rc_prev"])
+            self.learned.have_prev = snap["have_prev"]
+        self.cg, self.relres = [], []
+
+
+def timed_steps(loop, steps, world, dev):
+    """K steps between a barrier + synchronize on both sides, CUDA events on the stream."""
+    import torch
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(loop.stream)
+    for _ in range(steps):
+        loop.step()
+    e1.record(loop.stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    return max_over_ranks(e0.elapsed_time(e1), world)
+
+
+def secondary_size(args, n2, stream, dev, world):
+    """ms per optimisation iteration of a second cell size (the metric names 256^3 and
+    512^3): 3 warm-up steps (the first cold), 5 timed, same workload otherwise."""
+    import torch
+    loop = Loop(args, n2, args.seed, stream, dev)
+    cold = None
+    for w in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        loop.step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if w == 0:
+            cold = e0.elapsed_time(e1)
+    loop.cg, loop.relres = [], []
+    steps = 5
+    t = timed_steps(loop, steps, world, dev)
+    out = {"n": n2, "elements": n2 ** 3, "ms_per_step": t / steps, "steps": steps, "warmup": 3,
+           "cold_first_iteration_ms": cold, "cg_iterations_per_step": [max(c) for c in loop.cg],
+           "max_final_relres": max(loop.relres)}
+    del loop
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
 
     from paper_2301_08911_gb300 import binding
-    from synthetic import smoothed_threshold_density
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
-    rho0 = smoothed_threshold_density(n, args.vf, args.seed + rank)
     stream = torch.cuda.current_stream(dev)
-    hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream, smoother=args.smoother,
-                                 precision=args.precision)
-    r = torch.from_numpy(rho0).to(dev)
-    rt = torch.empty_like(r)
-    s = torch.empty_like(r)
-    dc = torch.empty_like(r)
-    beta = 0.8
-    state = {"it": 0, "cg": [], "relres": []}
+    # measured FP32 peaks (scalar FMA and two-lane f32x2), the ALU roofline's denominators
+    fp32_peak = {"scalar_tflops": binding.probe_fp32_peak(False), "f32x2_tflops": binding.probe_fp32_peak(True)}
+    loop = Loop(args, n, args.seed + rank, stream, dev)
+    hom = loop.hom
     tuning = None
     if args.autotune:
-        hom.filter(2.0, r, rt)
-        hom.set_density(rt)
+        hom.filter(2.0, loop.r, loop.rt)
+        hom.set_density(loop.rt)
         choice, times = hom.autotune(retime=True)
         tuning = {"cases_per_thread": choice[0], "threads_per_block": choice[1],
                   "ms_per_sweep": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times.items()}}
-    learned, net_info = None, None
+    net_info = None
     if args.warm_start != "previous":
         net, s_u, net_info = train_warm_start(args, dev, stream)
-        learned = LearnedStart(args, hom, net, s_u, dev)
-
-    def step():
-        hom.filter(2.0, r, rt)
-        hom.set_density(rt)
-        if learned is not None:
-            learned(rt)
-        its, rel, _ = hom.solve_cases(args.tol, args.max_iters, warm_start=True, raise_on_noconv=False)
-        C = hom.CH()
-        f, g = binding.objective(args.objective, C, state["it"], beta)
-        hom.sensitivity(g, s)
-        hom.filter(2.0, s, dc)
-        if args.sym != "none":
-            hom.symmetrize(args.sym, dc, dc)
-        hom.update(dc, r, args.vf)
-        if args.sym != "none":
-            hom.symmetrize(args.sym, r, r)
-        state["it"] += 1
-        state["cg"].append(its)
-        state["relres"].append(max(rel))
-        return f
+        loop.learned = LearnedStart(args, hom, net, s_u, dev)
 
     # warm-up (the first one is the cold solve from zero displacement)
     cold_ms = None
     for w in range(args.warmup):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        step()
+        loop.step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
         if w == 0:
             cold_ms = e0.elapsed_time(e1)
-    state["cg"].clear()
-    state["relres"].clear()
+    snap = loop.snapshot()
+    loop.restore(snap)
 
-    # timed region
-    barrier(world)
-    torch.cuda.synchronize(dev)
+    # timed region: device time of K steps, no per-launch instrumentation
     sampler = ClockSampler(local)
     sampler.start()
-    hom.profile(True)
-    launches0 = hom.launch_count + (learned.net.launch_count + learned.launches if learned else 0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    barrier(world)
-    launches = hom.launch_count + (learned.net.launch_count + learned.launches if learned else 0) - launches0
-    n_timed = len(state["cg"])
-    prof = hom.profile_read()
-    hom.profile(False)
+    launches0 = loop.launches()
+    t_ms = timed_steps(loop, args.steps, world, dev)
+    launches = loop.launches() - launches0
     clocks = sampler.stop()
-    t_ms = max_over_ranks(e0.elapsed_time(e1), world)
     ms_step = t_ms / args.steps
+    cg_timed = [list(c) for c in loop.cg]
+    relres_timed = list(loop.relres)
 
-    # end to end through the public API with host buffers: pinned host density in, new
-    # density and C^H out, every step
+    # end to end through the public API with host buffers, replaying the same K steps:
+    # every step copies its density in from pinned host memory and the new density and C^H
+    # out to the host
     e2e = None
     if not args.no_e2e:
-        host_rho = torch.from_numpy(r.cpu().numpy()).pin_memory()
+        loop.restore(snap)
+        host_rho = torch.from_numpy(loop.r.cpu().numpy()).pin_memory()
         barrier(world)
         torch.cuda.synchronize(dev)
         h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         h0.record(stream)
-        n_before = len(state["cg"])
         for _ in range(args.steps):
-            r.copy_(host_rho, non_blocking=True)
-            step()
-            host_rho.copy_(r, non_blocking=True)
+            loop.r.copy_(host_rho, non_blocking=True)
+            loop.step()
+            host_rho.copy_(loop.r, non_blocking=True)
         h1.record(stream)
         torch.cuda.synchronize(dev)
         barrier(world)
         te = max_over_ranks(h0.elapsed_time(h1), world)
         e2e = {"value": te / args.steps, "unit": "ms", "h2d_bytes_per_step": 4 * n ** 3,
                "d2h_bytes_per_step": 4 * n ** 3 + 36 * 8,
-               "note": "the next K iterations after the timed ones, density through pinned host memory",
-               "cg_iterations_per_step": [max(c) for c in state["cg"][n_before:]]}
+               "note": "the same K steps as the timed region, replayed from an exact snapshot; density in "
+                       "from and out to pinned host memory every step, C^H to the host",
+               "replays_timed_steps": [list(c) for c in loop.cg] == cg_timed}
+
+    # kernel breakdown: a separate replay of the timed steps with CUDA events around every launch
+    prof_steps = min(args.steps, max(1, args.profile_steps))
+    loop.restore(snap)
+    torch.cuda.synchronize(dev)
+    hom.profile(True)
+    for _ in range(prof_steps):
+        loop.step()
+    prof = hom.profile_read()
+    hom.profile(False)
+    prof_same = [list(c) for c in loop.cg] == cg_timed[:prof_steps]
+
+    second = None
+    if args.second_n and args.second_n != n and world == 1:
+        del snap
+        torch.cuda.empty_cache()
+        second = secondary_size(args, args.second_n, stream, dev, world)
 
     if rank != 0:
         return 0
 
-    # dominant kernel and its roofline
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    kc, (kn, kms) = dom
     peak_hbm, peak_src = measured_peaks()
-    nbytes, nflops = algorithmic_work(kc, n, args.sweeps or 1)
-    roofline = None
-    if nbytes is not None and kn > 0:
-        avg_s = kms / kn / 1000.0
-        sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-        alu_peak = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12      # TFLOP/s FP32
-        t_hbm = nbytes / (peak_hbm * 1e9)
-        t_alu = nflops / (alu_peak * 1e12)
-        traffic = recorded_traffic(kc, n)
-        if t_hbm >= t_alu:
-            ach = nbytes / avg_s / 1e9
-            roofline = {"bound": "hbm", "kernel": kc, "achieved": ach, "peak": peak_hbm, "unit": "GB/s",
-                        "frac": ach / peak_hbm, "traffic": traffic, "peak_source": peak_src,
-                        "bytes_per_launch": nbytes, "avg_launch_ms": kms / kn}
-        else:
-            ach = nflops / avg_s / 1e12
-            roofline = {"bound": "alu", "kernel": kc, "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s",
-                        "frac": ach / alu_peak, "traffic": traffic,
-                        "peak_source": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_mhz:.0f} MHz",
-                        "flops_per_launch": nflops, "bytes_per_launch": nbytes,
-                        "hbm_frac": nbytes / avg_s / 1e9 / peak_hbm, "avg_launch_ms": kms / kn}
+    sweeps = args.sweeps or 1
+    alu_peak = fp32_peak["scalar_tflops"]
+    alu_src = "measured: FP32 FMA probe (homo_probe_fp32_peak, scalar fma.rn.f32)"
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    roofline = roofline_of(dom[0], dom[1][0], dom[1][1], n, sweeps, peak_hbm, peak_src, alu_peak, alu_src)
+    stencil = {}
+    for kc in STENCIL_CLASSES:
+        kn, kms = prof.get(kc, (0, 0.0))
+        r = roofline_of(kc, kn, kms, n, sweeps, peak_hbm, peak_src, alu_peak, alu_src)
+        if r is not None:
+            stencil[kc] = {k: r[k] for k in ("avg_launch_ms", "launches", "hbm_gbs", "hbm_frac", "alu_tflops",
+                                             "alu_frac", "bytes_per_launch", "flops_per_launch", "bound")}
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        reps = 2
-        times = oracle_sample(args.sample_n, args.vf, args.objective, reps, args.seed)
-        scale = (n ** 3) / (args.sample_n ** 3)
-        cpu = {"value": 1000.0 * statistics.mean(times) * scale, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"{reps} oracle iterations at {args.sample_n}^3 (FP64 numpy/scipy, sparse LU), "
-                         f"single thread, scaled linearly by element count to {n}^3 (lower bound)"}
+        cpu = oracle_baseline(args, n)
 
-    cg = np.array(state["cg"][:n_timed])
+    cg = np.array(cg_timed)
     line = {
         "metric": METRIC,
         "value": ms_step, "unit": "ms", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -617,13 +777,18 @@ def run_ours(args, rank, world, local):
         "vs_baseline": (ms_step / PAPER_512_BULK_MS) if (n == 512 and args.objective == "bulk"
                                                           and abs(args.vf - 0.3) < 1e-9) else None,
         "dtype": "f32", "data": "synthetic", "config": config_dict(args),
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+        "roofline": roofline, "stencil": stencil, "fp32_peak": fp32_peak,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
         "gpu_launches": launches,
         "solver": {"cold_first_iteration_ms": cold_ms,
                    "cg_iterations_per_step": cg.max(axis=1).tolist() if cg.size else [],
-                   "max_final_relres": max(state["relres"][:n_timed]) if state["relres"] else None},
-        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]},
+                   "max_final_relres": max(relres_timed) if relres_timed else None},
+        "kernels": {"steps": prof_steps, "replays_timed_steps": prof_same,
+                    "note": "separate replay of the first timed steps with CUDA events around every launch",
+                    **{k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}},
     }
+    if second is not None:
+        line["second_size"] = second
     if net_info is not None:
         line["warm_start"] = dict(mode=args.warm_start, **net_info)
     if tuning is not None:

@@ -247,7 +247,7 @@ def macro_strain_loads_at_vertices(n: int, Ee: np.ndarray, Ke: np.ndarray, chi: 
 
 
 def homogenize(rho_t: np.ndarray, n: int, E0: float = 1.0, nu: float = 0.3, p: float = 3.0,
-               Emin: float = 1e-9, method: str = "lu") -> dict:
+               Emin: float = 1e-9, method: str = "lu", tol: float = 1e-11) -> dict:
     """Solve the 6 cell problems for the physical density rho_t and return C^H and its parts."""
     h = 1.0 / n
     Ke = ke_hex8(1.0, nu, h)
@@ -255,7 +255,7 @@ def homogenize(rho_t: np.ndarray, n: int, E0: float = 1.0, nu: float = 0.3, p: f
     chi = macro_strain_displacements(h)
     K = assemble_K(n, Ee, Ke)
     f = macro_strain_loads(n, Ee, Ke, chi)
-    u = solve_cases(K, f, method)
+    u = solve_cases(K, f, method, tol)
     q = element_energies(n, u, Ke, chi)
     C = homogenized_tensor(Ee, q)
     return {"C": C, "u": u, "q": q, "E": Ee, "f": f, "K": K, "Ke": Ke, "chi": chi, "h": h}

@@ -89,12 +89,12 @@ def optimization_iteration(rho: np.ndarray, n: int, volfrac: float, kind: str = 
                            iteration: int = 0, radius: float = 2.0, E0: float = 1.0,
                            nu: float = 0.3, p: float = 3.0, Emin: float = 1e-9,
                            move: float = 0.05, eta: float = 0.5, rho_min: float = 1e-3,
-                           method: str = "lu", sym: str | None = None) -> dict:
+                           method: str = "lu", sym: str | None = None, tol: float = 1e-11) -> dict:
     """One iteration of the loop of Sec. 5.2: filter -> SIMP -> 6 solves -> C^H -> f ->
     sensitivity -> filter adjoint (the filter itself) -> [symmetrise the sensitivity] ->
     OC update -> [symmetrise the density]; sym: None or a kind of Sec. 6.1."""
     rho_t = cone_filter(rho, n, radius)
-    hom = homogenize(rho_t, n, E0, nu, p, Emin, method)
+    hom = homogenize(rho_t, n, E0, nu, p, Emin, method, tol)
     f, g = objective(kind, hom["C"], iteration)
     s = sensitivity(rho_t, hom["q"], g, p, E0, Emin)
     dc = cone_filter(s, n, radius)
