@@ -755,8 +755,13 @@ def run_ours(args, rank, world, local):
     sweeps = args.sweeps or 1
     alu_peak = fp32_peak["scalar_tflops"]
     alu_src = "measured: FP32 FMA probe (homo_probe_fp32_peak, scalar fma.rn.f32)"
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    roofline = roofline_of(dom[0], dom[1][0], dom[1][1], n, sweeps, peak_hbm, peak_src, alu_peak, alu_src)
+    # the dominant kernel class among those with an algorithmic work model (the finest
+    # level's stencil and smoother classes and the element kernel)
+    modelled = {k: v for k, v in prof.items() if v[0] > 0 and algorithmic_work(k, n, sweeps)[0] is not None}
+    roofline = None
+    if modelled:
+        dom = max(modelled.items(), key=lambda kv: kv[1][1])
+        roofline = roofline_of(dom[0], dom[1][0], dom[1][1], n, sweeps, peak_hbm, peak_src, alu_peak, alu_src)
     stencil = {}
     for kc in STENCIL_CLASSES:
         kn, kms = prof.get(kc, (0, 0.0))

@@ -18,7 +18,16 @@ constexpr int EX = TX + 1, EY = TY + 1;        // element moduli tile
 constexpr int EPLANE = EX * EY;                // 297
 constexpr int kTiledThreads = TX * TY;         // 256
 constexpr int kUSlots = 4, kESlots = 3;
-constexpr int kUPlaneFloats = kPlanes * PLANE;
+// Each halo site holds its 18 values (6 cases x 3 components) in kCh consecutive floats,
+// ordered so that the two cases of a pair are adjacent: channel 6p + 2k + l holds case
+// 2p + l, component k. A neighbour's 9 case pairs are then 9 8-byte shared-memory loads
+// straight into f32x2 registers; with the 72-byte site stride the 8-byte loads of 16
+// consecutive sites fall on distinct banks.
+constexpr int kCh = 18;
+constexpr int kUPlaneFloats = kCh * PLANE;
+constexpr int kEFloats = (kESlots * EPLANE + 1) / 2 * 2;   // keeps the low-part bank 8-byte aligned
+
+__host__ __device__ constexpr int chan(int q) { return 6 * ((q / 3) / 2) + 2 * (q % 3) + (q / 3) % 2; }
 
 static_assert(PLANE > kTiledThreads && PLANE <= 2 * kTiledThreads, "two load sites per thread");
 static_assert(EPLANE > kTiledThreads && EPLANE <= 2 * kTiledThreads, "two modulus sites per thread");
@@ -77,8 +86,8 @@ __device__ __forceinline__ void issue_u_plane(const float* __restrict__ u, size_
   const float* g = u + zoff;
 #pragma unroll
   for (int q = 0; q < kPlanes; ++q) {
-    cp_async4(dst + q * PLANE + threadIdx.x, g + q * N + s.u0);
-    if (s.u1 >= 0) cp_async4(dst + q * PLANE + threadIdx.x + kTiledThreads, g + q * N + s.u1);
+    cp_async4(dst + threadIdx.x * kCh + chan(q), g + q * N + s.u0);
+    if (s.u1 >= 0) cp_async4(dst + (threadIdx.x + kTiledThreads) * kCh + chan(q), g + q * N + s.u1);
   }
 }
 
@@ -86,6 +95,14 @@ __device__ __forceinline__ void issue_e_plane(const float* __restrict__ E, size_
                                               float* __restrict__ dst) {
   cp_async4(dst + threadIdx.x, E + zoff + s.e0);
   if (s.e1 >= 0) cp_async4(dst + threadIdx.x + kTiledThreads, E + zoff + s.e1);
+}
+
+// The 9 case pairs of one site: 9 8-byte loads (kCh * 4 = 72 bytes per site: every site,
+// slot and bank starts on an 8-byte boundary).
+__device__ __forceinline__ void load_pairs(const float* site, f32x2 (&pr)[9]) {
+  const unsigned long long* p2 = reinterpret_cast<const unsigned long long*>(site);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) pr[i] = p2[i];
 }
 
 // MODE 1: out = K u in difference form (sum_d A_d (u_(v+d) - u_v)) with partials of the
@@ -111,9 +128,9 @@ __global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
                  double* __restrict__ part, const double* __restrict__ bmean, float c0, float c1) {
   constexpr bool kLo = MODE == 2;
   extern __shared__ float sm[];
-  float* su = sm;                                   // kUSlots x 18 x PLANE
+  float* su = sm;                                   // kUSlots x PLANE x kCh
   float* se = sm + kUSlots * kUPlaneFloats;         // kESlots x EPLANE
-  float* sl = se + kESlots * EPLANE;                // low parts (MODE 2): kUSlots x 18 x PLANE
+  float* sl = se + kEFloats;                        // low parts (MODE 2): kUSlots x PLANE x kCh
   const size_t N = static_cast<size_t>(n) * n * n;
   const size_t nn = static_cast<size_t>(n) * n;
   const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
@@ -160,19 +177,17 @@ __global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
         Et[t] = ((t >> 2) ? e0 : em)[(ty + ((t >> 1) & 1)) * EX + tx + (t & 1)];
       const int cidx = (ty + 1) * HX + tx + 1;
       constexpr bool kDiff = MODE == 1 || MODE == 2;
-      float own[kPlanes], ownlo[kLo ? kPlanes : 1];
-      if (kDiff) {
-#pragma unroll
-        for (int q = 0; q < kPlanes; ++q) own[q] = su[s0 + q * PLANE + cidx];
-      }
-      if (kLo) {
-#pragma unroll
-        for (int q = 0; q < kPlanes; ++q) ownlo[kLo ? q : 0] = sl[s0 + q * PLANE + cidx];
-      }
+      // the 6 cases advance in pairs (2p, 2p + 1) on the two lanes of f32x2 registers;
+      // every lane is rounded as the scalar chain in the same order would be
+      constexpr int kPairs = kCases / 2;
+      // pair j = 3p + k (cases 2p, 2p + 1, component k) sits at channels 2j, 2j + 1
+      f32x2 own[3 * kPairs], ownlo[3 * kPairs];
+      if (kDiff) load_pairs(su + s0 + cidx * kCh, own);
+      if (kLo) load_pairs(sl + s0 + cidx * kCh, ownlo);
       constexpr bool kCheb = MODE == 4 || MODE == 5 || MODE == 6;
-      float acc[kPlanes];
+      f32x2 accp[3 * kPairs];
 #pragma unroll
-      for (int q = 0; q < kPlanes; ++q) acc[q] = 0.f;
+      for (int q = 0; q < 3 * kPairs; ++q) accp[q] = 0ull;
       float S[9];
 #pragma unroll
       for (int d = 0; d < 27; ++d) {
@@ -184,21 +199,38 @@ __global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
 #pragma unroll
           for (int q = 0; q < 9; ++q) S[q] = A[q];
         }
-        const int off = (dz < 0 ? sm1 : (dz == 0 ? s0 : sp1)) + cidx + dy * HX + dx;
+        f32x2 Ap[9];
 #pragma unroll
-        for (int c = 0; c < kCases; ++c) {
-          float uu[3];
+        for (int e = 0; e < 9; ++e) Ap[e] = pack2(A[e], A[e]);
+        const int off = (dz < 0 ? sm1 : (dz == 0 ? s0 : sp1)) + (cidx + dy * HX + dx) * kCh;
+        f32x2 uv[3 * kPairs];
+        load_pairs(su + off, uv);
+        if (kDiff) {
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            uu[k] = su[off + (3 * c + k) * PLANE];
-            if (kDiff) uu[k] -= own[3 * c + k];
-            if (kLo) uu[k] += sl[off + (3 * c + k) * PLANE] - ownlo[kLo ? 3 * c + k : 0];
-          }
+          for (int j = 0; j < 3 * kPairs; ++j) uv[j] = fsub2(uv[j], own[j]);
+        }
+        if (kLo) {
+          f32x2 lv[3 * kPairs];
+          load_pairs(sl + off, lv);
+#pragma unroll
+          for (int j = 0; j < 3 * kPairs; ++j) uv[j] = fadd2(uv[j], fsub2(lv[j], ownlo[j]));
+        }
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
 #pragma unroll
           for (int r = 0; r < 3; ++r)
-            acc[3 * c + r] = fmaf(A[3 * r], uu[0], fmaf(A[3 * r + 1], uu[1], fmaf(A[3 * r + 2], uu[2], acc[3 * c + r])));
+            accp[3 * p + r] = ffma2(Ap[3 * r], uv[3 * p], ffma2(Ap[3 * r + 1], uv[3 * p + 1],
+                                    ffma2(Ap[3 * r + 2], uv[3 * p + 2], accp[3 * p + r])));
         }
       }
+      float acc[kPlanes], own1[kDiff ? kPlanes : 1];
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          unpack2(accp[3 * p + r], acc[6 * p + r], acc[6 * p + 3 + r]);
+          if (kDiff) unpack2(own[3 * p + r], own1[kDiff ? 6 * p + r : 0], own1[kDiff ? 6 * p + 3 + r : 0]);
+        }
       const size_t v = static_cast<size_t>(z) * nn + static_cast<size_t>(y) * n + x;
       if (kCheb) {
         // residual, block-diagonal solve, Chebyshev update
@@ -209,7 +241,7 @@ __global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
 #pragma unroll
         for (int q = 0; q < kPlanes; ++q) {
           const size_t o = q * N + v;
-          const float uc = su[s0 + q * PLANE + cidx];
+          const float uc = su[s0 + cidx * kCh + chan(q)];
           if (MODE == 4) out[o] = fmaf(c0, acc[q], uc);
           else if (MODE == 5) out[o] = fmaf(c1, acc[q], fmaf(c0, uc - out[o], uc));
           else out[o] = fmaf(c1, acc[q], fmaf(c0, uc, uc));
@@ -222,7 +254,7 @@ __global__ void __launch_bounds__(kTiledThreads, MODE == 2 ? 1 : 2)
           if (MODE == 3) val = (__ldg(b + o) - (bmean ? static_cast<float>(bmean[q]) : 0.f)) - val;
           if (MODE == 2) val = __ldg(b + o) - val;
           out[o] = val;
-          if (MODE == 1) red[q / 3] = fmaf(own[q], val, red[q / 3]);
+          if (MODE == 1) red[q / 3] = fmaf(own1[kDiff ? q : 0], val, red[q / 3]);
           if (MODE == 2) red[q / 3] = fmaf(val, val, red[q / 3]);
           if (kDiff) red[kCases + q] += val;
         }
@@ -248,7 +280,7 @@ int tiled_zchunk(int n) {
 }  // namespace
 
 size_t tiled_smem_bytes(int mode) {
-  return sizeof(float) * (kUSlots * kUPlaneFloats * (mode == 2 ? 2 : 1) + kESlots * EPLANE);
+  return sizeof(float) * (kUSlots * kUPlaneFloats * (mode == 2 ? 2 : 1) + kEFloats);
 }
 
 int tiled_grid_blocks(int n) {
