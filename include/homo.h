@@ -469,6 +469,13 @@ int homo_nn_conv3d(int n, int c_in, const void* x, const void* w, const float* b
                    const void* mask, int epilogue, void* out, float* out_planes, const double* scale,
                    void* stream);
 
+/* The layer runs on the tcgen05 tensor cores: one thread per CTA issues the MMAs and the
+ * CTA waits for their completion on an mbarrier with a bounded number of polls. Returns
+ * the number of tile waits that ran out since the last call (0 in normal operation; the
+ * outputs of such a tile are not written) and resets it; -1 if it cannot be read.
+ * Synchronous (reads a device counter). */
+int homo_nn_tc_timeouts(void);
+
 /* Weight and bias gradients of one layer: dw[t][o][i] = sum_v dy[v,o] x[wrap(v + d_t), i],
  * db[o] = sum_v dy[v,o] (FP32, summed in a fixed order: deterministic). x: n^3 x c_in
  * BF16, dy: n^3 x 32 BF16; scratch: device floats, at least homo_nn_wgrad_scratch(n, c_in). */

@@ -69,6 +69,7 @@ SIGNATURES = {
     "homo_save_displacement": (ctypes.c_int, [_vp, _vp, _vp]),
     "homo_restore_displacement": (ctypes.c_int, [_vp, _vp, _vp]),
     "homo_probe_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "homo_nn_tc_timeouts": (ctypes.c_int, []),
     "homo_get_stencil": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "homo_restrict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "homo_prolong": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -433,6 +434,11 @@ def nn_conv3d(n: int, c_in: int, x, w, bias=None, res=None, mask=None, epilogue:
     _nn_check(lib.homo_nn_conv3d(n, c_in, _vp(_dptr(x)), _vp(_dptr(w)), _opt(bias), _opt(res), _opt(mask),
                                  NN_EPILOGUES[epilogue], _opt(out), _opt(out_planes), _scale6(scale),
                                  _vp(_stream_of(stream))), "homo_nn_conv3d")
+
+
+def nn_tc_timeouts() -> int:
+    """Tensor-core convolution tiles whose completion wait ran out since the last call."""
+    return load_library().homo_nn_tc_timeouts()
 
 
 def nn_wgrad_scratch(n: int, c_in: int) -> int:

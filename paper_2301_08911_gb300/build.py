@@ -22,7 +22,7 @@ LIB = os.path.join(BUILD, "libhomo.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["element.cu", "fine.cu", "fine_gs.cu", "fine_tiled.cu", "coarse.cu", "vec.cu", "api.cu", "learned.cu", "probe.cu",
+SOURCES = ["element.cu", "fine.cu", "fine_gs.cu", "fine_tiled.cu", "coarse.cu", "vec.cu", "api.cu", "learned.cu", "conv_tc.cu", "probe.cu",
            "net.cu"]
 
 

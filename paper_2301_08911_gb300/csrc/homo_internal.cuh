@@ -185,6 +185,11 @@ void build_element_matrix(double nu, KeParam& ke, LoadParam& ld, ChiParam& chi);
 void build_level1_tables(const KeParam& ke, float* host_Bf /* 8*576 */);
 int build_filter_param(double radius, FilterParam& fp);
 
+// ---- warm-start network convolution on the tcgen05 tensor cores (conv_tc.cu) ----
+cudaError_t conv3d_tc(int n, int cin, int epi, const void* x, const void* w, const float* bias, const void* res,
+                      const void* mask, void* out, float* outf, const double* scale, cudaStream_t s);
+int conv3d_tc_take_timeouts();
+
 // ---- launchers (fine.cu) ----
 cudaError_t launch_simp(const float* rho_in, float* rho_out, float* E, size_t N, float p,
                         float E0, float Emin, cudaStream_t s);

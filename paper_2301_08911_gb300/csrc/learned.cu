@@ -2,16 +2,12 @@
 // density of a cell to the 18 displacement planes of its 6 load cases (not part of the
 // paper's method, which warm-starts from the previous iterate, Sec. 3.3).
 //
-// Every convolution is an implicit GEMM on the tensor cores: M = voxels, N = 32 output
-// channels, K = 27 taps x c_in, BF16 operands, FP32 accumulation (mma.sync m16n8k16).
-// A persistent CTA keeps the layer's weights in shared memory and walks 16 x 4 x 2
-// voxel tiles; each tile's periodic halo box (18 x 6 x 4 voxels, all channels) is staged
-// with 16-byte asynchronous copies, and each warp computes two 16-voxel rows x 32
-// channels from it. The epilogue adds bias / residual, applies the ReLU or the ReLU
-// mask of a backward pass, and writes BF16 voxel-major activations or FP32 planes.
-// The weight gradient contracts over voxels: per tap and voxel chunk a CTA stages the
-// transposed operands and accumulates a 32 x c_in block, and a second kernel sums the
-// chunks in a fixed order (deterministic).
+// The layers' forward and backward-data convolutions run on the tcgen05 tensor cores
+// (conv_tc.cu). This file holds the rest of the network's arithmetic: the weight gradient,
+// which contracts over voxels (per tap and voxel chunk a CTA stages the transposed
+// operands and accumulates a 32 x c_in block with BF16 mma.sync, FP32 accumulation; a
+// second kernel sums the chunks in a fixed order, so it is deterministic), the input
+// features, pooling, the MSE loss and its gradient, Adam, and the BF16 weight packing.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -28,41 +24,10 @@ namespace {
 
 constexpr int kC = HOMO_NN_CHANNELS;    // output channels of every layer (32)
 constexpr int kTaps = 27;
-constexpr int TX = 16, TY = 4, TZ = 2;  // voxels per conv tile (x, y, z)
-constexpr int BX = TX + 2, BY = TY + 2, BZ = TZ + 2;
-constexpr int kBoxVox = BX * BY * BZ;   // 432
-constexpr int kConvThreads = 128;       // 4 warps; warp w owns rows y = w, z = 0 and 1
-static_assert(kConvThreads / 32 == TY && TZ == 2, "warp to row mapping");
 
-template <int CIN>
-struct ConvShape {
-  static constexpr int XS = CIN + 8;    // bf16 per staged voxel: rows 16 B apart mod 128 B
-  static constexpr int WS = CIN + 8;    // bf16 per weight row (tap, o)
-  static constexpr int kBoxBytes = kBoxVox * XS * 2;
-  static constexpr int kWBytes = kTaps * kC * WS * 2;
-  static constexpr int kBytes = kBoxBytes + kWBytes;
-  static_assert(kBoxBytes % 16 == 0 && (XS * 2) % 16 == 0 && (WS * 2) % 16 == 0, "16-byte copies");
-};
-
-// Output scale of each load case: plane p = 3 case + component takes s[p / 3].
-struct CaseScale {
-  float s[6];
-};
-
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t ld32(const __nv_bfloat16* p) {
   return *reinterpret_cast<const uint32_t*>(p);
-}
-__device__ __forceinline__ float2 unpack2(uint32_t u) {
-  __nv_bfloat162 h;
-  memcpy(&h, &u, 4);
-  return __bfloat1622float2(h);
 }
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
   const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);   // a -> low half
@@ -83,132 +48,6 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
 __device__ __forceinline__ int wrapc(int a, int n) {
   a %= n;
   return a < 0 ? a + n : a;
-}
-
-template <int CIN, int EPI>
-__global__ void __launch_bounds__(kConvThreads, 2)
-    k_conv3d(int n, int tiles_x, int tiles_y, int ntiles, const __nv_bfloat16* __restrict__ x,
-             const __nv_bfloat16* __restrict__ w, const float* __restrict__ bias,
-             const __nv_bfloat16* __restrict__ res, const __nv_bfloat16* __restrict__ mask,
-             __nv_bfloat16* __restrict__ out, float* __restrict__ outf, CaseScale sc) {
-  using S = ConvShape<CIN>;
-  extern __shared__ __align__(16) unsigned char smem[];
-  __nv_bfloat16* box = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* ws = reinterpret_cast<__nv_bfloat16*>(smem + S::kBoxBytes);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, t4 = lane & 3;
-  const size_t N = static_cast<size_t>(n) * n * n;
-  constexpr int kChunks = CIN / 8;       // 16-byte pieces per voxel / weight row
-
-  for (int c = tid; c < kTaps * kC * kChunks; c += kConvThreads) {
-    const int row = c / kChunks, ch = c - row * kChunks;
-    cp_async16(ws + row * S::WS + ch * 8, w + static_cast<size_t>(row) * CIN + ch * 8);
-  }
-  cp_async_commit();                     // completed by the first tile's wait
-
-  float bo[4][2];                        // bias of this thread's output columns
-  float so[4][2];                        // output scale of each (planes epilogues)
-#pragma unroll
-  for (int nt = 0; nt < 4; ++nt) {
-    const int o = nt * 8 + 2 * t4;
-    bo[nt][0] = (EPI != HOMO_NN_MASK && bias) ? bias[o] : 0.f;
-    bo[nt][1] = (EPI != HOMO_NN_MASK && bias) ? bias[o + 1] : 0.f;
-    so[nt][0] = o < 18 ? sc.s[o / 3] : 0.f;
-    so[nt][1] = o + 1 < 18 ? sc.s[(o + 1) / 3] : 0.f;
-  }
-
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int tx = tile % tiles_x, rest = tile / tiles_x;
-    const int ty = rest % tiles_y, tz = rest / tiles_y;
-    const int x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
-    __syncthreads();                     // every warp is done with the previous box
-    for (int c = tid; c < kBoxVox * kChunks; c += kConvThreads) {
-      const int bv = c / kChunks, ch = c - bv * kChunks;
-      const int bx = bv % BX, by = (bv / BX) % BY, bz = bv / (BX * BY);
-      const size_t gv = static_cast<size_t>(wrapc(x0 - 1 + bx, n)) +
-                        static_cast<size_t>(n) * (wrapc(y0 - 1 + by, n) +
-                                                  static_cast<size_t>(n) * wrapc(z0 - 1 + bz, n));
-      cp_async16(box + bv * S::XS + ch * 8, x + gv * CIN + ch * 8);
-    }
-    cp_async_commit();
-    cp_async_wait_all();
-    __syncthreads();
-
-    float acc[2][4][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[mt][nt][q] = 0.f;
-
-#pragma unroll 1
-    for (int tap = 0; tap < kTaps; ++tap) {
-      const int dx = tap % 3, dy = (tap / 3) % 3, dz = tap / 9;   // offsets + 1
-#pragma unroll
-      for (int ks = 0; ks < CIN / 16; ++ks) {
-        uint32_t a[2][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-          // row r of this m-tile is output voxel (x0 + r, y0 + warp, z0 + mt); its tap
-          // neighbour sits at box (r + dx, warp + dy, mt + dz)
-          const __nv_bfloat16* r0 =
-              box + (((mt + dz) * BY + warp + dy) * BX + dx + g) * S::XS + ks * 16 + 2 * t4;
-          a[mt][0] = ld32(r0);
-          a[mt][1] = ld32(r0 + 8 * S::XS);
-          a[mt][2] = ld32(r0 + 8);
-          a[mt][3] = ld32(r0 + 8 * S::XS + 8);
-        }
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const __nv_bfloat16* wr = ws + (tap * kC + nt * 8 + g) * S::WS + ks * 16 + 2 * t4;
-          const uint32_t b0 = ld32(wr), b1 = ld32(wr + 8);
-          mma16816(acc[0][nt], a[0], b0, b1);
-          mma16816(acc[1][nt], a[1], b0, b1);
-        }
-      }
-    }
-
-    const int gy = y0 + warp;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt) {
-      const int gz = z0 + mt;
-      if (gz >= n || gy >= n) continue;
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int gx = x0 + g + 8 * half;
-        if (gx >= n) continue;
-        const size_t v = static_cast<size_t>(gx) + static_cast<size_t>(n) * (gy + static_cast<size_t>(n) * gz);
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          const int o = nt * 8 + 2 * t4;
-          float v0 = acc[mt][nt][2 * half] + bo[nt][0];
-          float v1 = acc[mt][nt][2 * half + 1] + bo[nt][1];
-          if (EPI == HOMO_NN_PLANES || EPI == HOMO_NN_PLANES_ADD) {
-            float* d0 = outf + static_cast<size_t>(o) * N + v;
-            float* d1 = d0 + N;
-            if (o < 18) *d0 = EPI == HOMO_NN_PLANES_ADD ? *d0 + so[nt][0] * v0 : so[nt][0] * v0;
-            if (o + 1 < 18) *d1 = EPI == HOMO_NN_PLANES_ADD ? *d1 + so[nt][1] * v1 : so[nt][1] * v1;
-            continue;
-          }
-          if (res) {
-            const float2 r = unpack2(ld32(res + v * kC + o));
-            v0 += r.x;
-            v1 += r.y;
-          }
-          if (EPI == HOMO_NN_RELU) {
-            v0 = fmaxf(v0, 0.f);
-            v1 = fmaxf(v1, 0.f);
-          } else {
-            const float2 m = unpack2(ld32(mask + v * kC + o));
-            v0 = m.x > 0.f ? v0 : 0.f;
-            v1 = m.y > 0.f ? v1 : 0.f;
-          }
-          *reinterpret_cast<uint32_t*>(out + v * kC + o) = pack2(v0, v1);
-        }
-      }
-    }
-  }
 }
 
 constexpr int kWgTile = 128;              // voxels per staged weight-gradient tile
@@ -440,25 +279,6 @@ int num_sms() {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-template <int CIN, int EPI>
-cudaError_t conv_launch(int n, const void* x, const void* w, const float* bias, const void* res, const void* mask,
-                        void* out, float* outf, const double* scale, cudaStream_t s) {
-  CaseScale sc;
-  for (int k = 0; k < 6; ++k) sc.s[k] = scale ? static_cast<float>(scale[k]) : 1.f;
-  using S = ConvShape<CIN>;
-  auto kern = k_conv3d<CIN, EPI>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::kBytes);
-  if (e != cudaSuccess) return e;
-  const int tiles_x = (n + TX - 1) / TX, tiles_y = (n + TY - 1) / TY, tiles_z = (n + TZ - 1) / TZ;
-  const long long ntiles = static_cast<long long>(tiles_x) * tiles_y * tiles_z;
-  const int grid = static_cast<int>(std::min<long long>(ntiles, 2LL * num_sms()));
-  kern<<<grid, kConvThreads, S::kBytes, s>>>(
-      n, tiles_x, tiles_y, static_cast<int>(ntiles), static_cast<const __nv_bfloat16*>(x),
-      static_cast<const __nv_bfloat16*>(w), bias, static_cast<const __nv_bfloat16*>(res),
-      static_cast<const __nv_bfloat16*>(mask), static_cast<__nv_bfloat16*>(out), outf, sc);
-  return cudaGetLastError();
-}
-
 struct WgradPlan {
   int ntiles, tiles_per_chunk, chunks;
 };
@@ -483,15 +303,7 @@ size_t wgrad_scratch_floats(int n, int cin) {
 // ---- launchers --------------------------------------------------------------------------
 cudaError_t nn_conv3d(int n, int cin, const void* x, const void* w, const float* bias, const void* res,
                       const void* mask, int epi, void* out, float* outf, const double* scale, cudaStream_t s) {
-#define HOMO_CONV_CASE(CI, EP) \
-  if (cin == CI && epi == EP) return conv_launch<CI, EP>(n, x, w, bias, res, mask, out, outf, scale, s);
-  HOMO_CONV_CASE(16, HOMO_NN_RELU)
-  HOMO_CONV_CASE(32, HOMO_NN_RELU)
-  HOMO_CONV_CASE(32, HOMO_NN_MASK)
-  HOMO_CONV_CASE(32, HOMO_NN_PLANES)
-  HOMO_CONV_CASE(32, HOMO_NN_PLANES_ADD)
-#undef HOMO_CONV_CASE
-  return cudaErrorInvalidValue;
+  return conv3d_tc(n, cin, epi, x, w, bias, res, mask, out, outf, scale, s);
 }
 
 cudaError_t nn_wgrad(int n, int cin, const void* x, const void* dy, float* dw, float* db, float* scratch,
@@ -584,6 +396,8 @@ bool conv_args_ok(int n, int c_in, const void* x, const void* w, const void* res
 }  // namespace
 
 extern "C" {
+
+int homo_nn_tc_timeouts(void) { return conv3d_tc_take_timeouts(); }
 
 int homo_nn_conv3d(int n, int c_in, const void* x, const void* w, const float* bias, const void* res,
                    const void* mask, int epilogue, void* out, float* out_planes, const double* scale,
