@@ -476,6 +476,12 @@ int homo_nn_conv3d(int n, int c_in, const void* x, const void* w, const float* b
  * Synchronous (reads a device counter). */
 int homo_nn_tc_timeouts(void);
 
+/* Exercises that bounded wait on its own: launches `blocks` CTAs (1..1024) that wait on an
+ * mbarrier nothing arrives on, each giving up after the same poll limit and counting one
+ * timeout (read with homo_nn_tc_timeouts). No tensor-core work is issued. For failure-
+ * detection tests; takes about a second. Synchronises the device. */
+int homo_nn_tc_wait_probe(int blocks);
+
 /* Weight and bias gradients of one layer: dw[t][o][i] = sum_v dy[v,o] x[wrap(v + d_t), i],
  * db[o] = sum_v dy[v,o] (FP32, summed in a fixed order: deterministic). x: n^3 x c_in
  * BF16, dy: n^3 x 32 BF16; scratch: device floats, at least homo_nn_wgrad_scratch(n, c_in). */

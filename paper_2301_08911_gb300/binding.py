@@ -70,6 +70,7 @@ SIGNATURES = {
     "homo_restore_displacement": (ctypes.c_int, [_vp, _vp, _vp]),
     "homo_probe_fp32_peak": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "homo_nn_tc_timeouts": (ctypes.c_int, []),
+    "homo_nn_tc_wait_probe": (ctypes.c_int, [ctypes.c_int]),
     "homo_get_stencil": (ctypes.c_int, [_vp, ctypes.c_int, _vp]),
     "homo_restrict": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "homo_prolong": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
@@ -439,6 +440,11 @@ def nn_conv3d(n: int, c_in: int, x, w, bias=None, res=None, mask=None, epilogue:
 def nn_tc_timeouts() -> int:
     """Tensor-core convolution tiles whose completion wait ran out since the last call."""
     return load_library().homo_nn_tc_timeouts()
+
+
+def nn_tc_wait_probe(blocks: int = 4):
+    """Run the bounded mbarrier wait against a barrier nothing arrives on (timeouts counted)."""
+    _nn_check(load_library().homo_nn_tc_wait_probe(blocks), "homo_nn_tc_wait_probe")
 
 
 def nn_wgrad_scratch(n: int, c_in: int) -> int:

@@ -310,6 +310,18 @@ __global__ void __launch_bounds__(kThreads, 2)
   }
 }
 
+// The bounded completion wait on an mbarrier that no one arrives on: every CTA gives up
+// after kWaitLimit polls and counts the timeout, the path a tile takes when its MMAs never
+// complete (no MMA is issued here, so nothing is left in flight).
+__global__ void k_wait_probe() {
+  __shared__ __align__(8) uint64_t bar;
+  const uint32_t b = smem_u32(&bar);
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(b) : "memory");
+  __syncthreads();
+  const bool ok = mbar_wait(b, 0);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicAdd(&g_conv_tc_timeouts, 1);
+}
+
 int g_sms = 0;
 
 int sm_count() {
@@ -357,6 +369,12 @@ cudaError_t conv3d_tc(int n, int cin, int epi, const void* x, const void* w, con
   HOMO_TC_CASE(32, HOMO_NN_PLANES_ADD)
 #undef HOMO_TC_CASE
   return cudaErrorInvalidValue;
+}
+
+cudaError_t conv3d_tc_wait_probe(int blocks) {
+  k_wait_probe<<<blocks, 32>>>();
+  const cudaError_t e = cudaGetLastError();
+  return e != cudaSuccess ? e : cudaDeviceSynchronize();
 }
 
 // Number of tiles whose completion wait ran out since the last call (and reset it).

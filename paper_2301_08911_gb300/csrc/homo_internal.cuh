@@ -189,6 +189,7 @@ int build_filter_param(double radius, FilterParam& fp);
 cudaError_t conv3d_tc(int n, int cin, int epi, const void* x, const void* w, const float* bias, const void* res,
                       const void* mask, void* out, float* outf, const double* scale, cudaStream_t s);
 int conv3d_tc_take_timeouts();
+cudaError_t conv3d_tc_wait_probe(int blocks);
 
 // ---- launchers (fine.cu) ----
 cudaError_t launch_simp(const float* rho_in, float* rho_out, float* E, size_t N, float p,

@@ -399,6 +399,11 @@ extern "C" {
 
 int homo_nn_tc_timeouts(void) { return conv3d_tc_take_timeouts(); }
 
+int homo_nn_tc_wait_probe(int blocks) {
+  if (blocks < 1 || blocks > 1024) return HOMO_EINVAL;
+  return cuda_status(conv3d_tc_wait_probe(blocks));
+}
+
 int homo_nn_conv3d(int n, int c_in, const void* x, const void* w, const float* bias, const void* res,
                    const void* mask, int epilogue, void* out, float* out_planes, const double* scale,
                    void* stream) {

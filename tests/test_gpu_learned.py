@@ -6,8 +6,10 @@ oracle in FP64, then both round the stored activations to BF16 at the same point
 stored BF16 value may therefore differ by one BF16 unit in the last place where the two
 sums straddle a rounding boundary (rare, counted below); FP32 outputs and weight
 gradients agree to the FP32 accumulation bound 1e-5 * (sum of |terms|).
-Grid sizes 4, 13 and 20 give one tile, ragged tiles in x, y and z (13 is odd) and
-several tiles with a ragged x tail (tile 16 x 4 x 2).
+Grid sizes 4, 13 and 20 give one ragged tile in x (the layer's tiles are 30 x 4 x 2
+voxels), ragged tiles in y and z (13 is odd) and several tiles in y and z; 36 adds a
+second x tile with a ragged tail (the weight gradient's 128-voxel tiles are ragged at every
+size).
 """
 import numpy as np
 import pytest
@@ -70,7 +72,7 @@ def _randn(shape, seed, s=1.0):
     return s * normal_field(int(np.prod(shape)), seed).reshape(shape)
 
 
-@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("n", SIZES + [36])
 @pytest.mark.parametrize("c_in", [16, 32])
 def test_conv_relu_with_bias_and_residual(B, n, c_in):
     N = n ** 3
@@ -87,7 +89,7 @@ def test_conv_relu_with_bias_and_residual(B, n, c_in):
     check_bf16(host(out2), L.bf16_round(np.maximum(L.conv3d(xh, wh, None, n), 0.0)), acc_bound(xh, wh, n))
 
 
-@pytest.mark.parametrize("n", SIZES)
+@pytest.mark.parametrize("n", SIZES + [36])
 def test_conv_mask_and_planes(B, n):
     N = n ** 3
     x, xh = bf16(_randn((N, 32), 11 + n))
@@ -296,3 +298,24 @@ def test_training_and_learned_warm_start(B):
         assert np.linalg.norm(hom.CH() - C_cold[i]) <= 1e-6 * np.linalg.norm(C_cold[i])
         print(f"cell {i}: energy error / zero start {np.round(ratio, 3)}, start residual {np.round(start, 3)}, "
               f"iterations cold {its_cold[i]} learned {its}")
+
+
+def test_tensor_core_wait_gives_up_and_reports(B):
+    """The layer's completion wait is bounded: against an mbarrier that no one arrives on,
+    every CTA gives up after its poll limit and counts one timeout, which the host reads;
+    the context stays usable and a following layer reports none."""
+    import time
+    B.nn_tc_timeouts()                                  # reset
+    t0 = time.perf_counter()
+    B.nn_tc_wait_probe(4)
+    waited = time.perf_counter() - t0
+    assert B.nn_tc_timeouts() == 4
+    assert waited < 60.0
+    n = 8
+    x, xh = bf16(_randn((n ** 3, 32), 91))
+    w, wh = bf16(_randn((27, 32, 32), 92, 0.1))
+    out = torch.empty((n ** 3, 32), dtype=torch.bfloat16, device="cuda")
+    B.nn_conv3d(n, 32, x, w, epilogue="relu", out=out)
+    check_bf16(host(out), L.bf16_round(np.maximum(L.conv3d(xh, wh, None, n), 0.0)), acc_bound(xh, wh, n))
+    assert B.nn_tc_timeouts() == 0
+    print(f"bounded wait gave up after {waited:.3f} s")
