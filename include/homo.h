@@ -479,7 +479,8 @@ int homo_nn_tc_timeouts(void);
 /* Exercises that bounded wait on its own: launches `blocks` CTAs (1..1024) that wait on an
  * mbarrier nothing arrives on, each giving up after the same poll limit and counting one
  * timeout (read with homo_nn_tc_timeouts). No tensor-core work is issued. For failure-
- * detection tests; takes about a second. Synchronises the device. */
+ * detection tests; takes about a second (each CTA polls 2^18 times). Synchronises the
+ * device. */
 int homo_nn_tc_wait_probe(int blocks);
 
 /* Weight and bias gradients of one layer: dw[t][o][i] = sum_v dy[v,o] x[wrap(v + d_t), i],

@@ -38,7 +38,7 @@ constexpr int kRows = 776;                                 // >= kRowPad + kBoxR
 constexpr int kPlaneBytes = kRows * 16;                    // one 8-channel chunk of every row
 constexpr int kThreads = 128;
 constexpr int kTmemCols = 64;                              // two 128 x 32 FP32 accumulators
-constexpr long long kWaitLimit = 1LL << 22;                // bounded mbarrier polls (~seconds)
+constexpr long long kWaitLimit = 1LL << 18;                // bounded mbarrier polls (~1 s on a GB300)
 
 static_assert(kRowPad + kBoxRows + 1 <= kRows, "guard rows");
 static_assert(kThreads == 4 * 32 && TYo == 4, "warp w owns output row y = w of each plane");

@@ -16,16 +16,8 @@ namespace {
 // once). Every variant (CASES, BLOCK) performs the same arithmetic per vertex and case in
 // the same order, so all give bitwise the same result; homo_autotune picks the fastest
 // for a grid size.
-// Register budgets (minimum resident blocks per SM): (3, 256) and (6, 128) 64 and 128
-// registers at 1024 / 512 threads per SM; (3, 128) trades occupancy for more loads in
-// flight per thread (85 registers, 768 threads); (6, 256) 128 registers at 512 threads.
 template <int CASES, int BLOCK>
-constexpr int gs_min_blocks() {
-  return CASES == 3 ? (BLOCK == 256 ? 4 : 6) : (BLOCK == 256 ? 2 : 4);
-}
-
-template <int CASES, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, gs_min_blocks<CASES, BLOCK>())
+__global__ void __launch_bounds__(BLOCK, (CASES == 3 ? 1024 : 512) / BLOCK)
     k_fine_gs(const __grid_constant__ KeParam K, const float* __restrict__ E, const float* __restrict__ f,
               float* __restrict__ u, int n, int colour, int first, const double* __restrict__ fmean) {
   constexpr int kGsCases = CASES;
