@@ -8,7 +8,10 @@ cell on a CPU, too long to repeat in every GPU test run, so its results are stor
   radius 2, rounded to FP32) and then read back in FP64 by the oracle;
 * per cell: C^H (Eq. 7), the certificate (true relative residual per case), and for the
   bulk (Eq. 19) and shear (Eq. 20) objectives the element sensitivities (Eq. 8-9) at a
-  fixed stride sample of 4096 elements, with the L2 norm and the sum of the full vector.
+  fixed stride sample of 4096 elements, with the L2 norm and the sum of the full vector
+  (oracle_64.json);
+* the full sensitivity vectors, rounded to FP32 (6e-8 relative, far below the 1e-6 bar
+  they are compared at), in oracle_64_sens.npz, keyed "<cell>_<objective>".
 
 Usage (repo root): python tests/golden/make_oracle_golden.py
 """
@@ -62,25 +65,31 @@ def cell_results(kind: str, n: int) -> dict:
     idx = sample_indices(n)
     out = {"C": C.tolist(), "relres": info["relres"].tolist(), "iterations": int(info["iterations"]),
            "sensitivity": {}}
+    full = {}
     for obj in ("bulk", "shear"):
         _, g = oracle.objective(obj, C)
         s = oracle.sensitivity(rho_t, q, g)
         out["sensitivity"][obj] = {"sample": [float("%.12g" % v) for v in s[idx]],
                                    "norm2": float(np.linalg.norm(s)), "sum": float(s.sum())}
-    return out
+        full[f"{kind}_{obj}"] = s.astype(np.float32)
+    return out, full
 
 
 def main() -> None:
     data = {"_source": "oracle/ (FP64, pcg_solve 'mg' to true relative residual 1e-11) via "
                        "tests/golden/make_oracle_golden.py",
             "n": N_CELL, "stride": STRIDE, "samples": SAMPLES, "cells": {}}
+    vectors = {}
     for kind in CELLS:
         print(kind, flush=True)
-        data["cells"][kind] = cell_results(kind, N_CELL)
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), f"oracle_{N_CELL}.json")
+        data["cells"][kind], full = cell_results(kind, N_CELL)
+        vectors.update(full)
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, f"oracle_{N_CELL}.json")
     with open(path, "w") as fh:
         json.dump(data, fh, separators=(",", ":"))
         fh.write("\n")
+    np.savez_compressed(os.path.join(here, f"oracle_{N_CELL}_sens.npz"), **vectors)
     print(path)
 
 

@@ -247,20 +247,21 @@ def _golden64():
 @pytest.mark.parametrize("kind", ["c1", "uniform"])
 def test_CH_and_sensitivities_match_stored_oracle_64(B, kind):
     """64^3 against the oracle's stored results (tests/golden/make_oracle_golden.py: certified
-    FP64 multigrid-preconditioned CG): C^H in full, sensitivities at 4096 stride-sampled
-    elements plus the norm and sum of the whole vector, at the 1e-6 bar.
+    FP64 multigrid-preconditioned CG): C^H in full, and the whole sensitivity vector at the
+    1e-6 bar in L2, every element of density >= 0.01 within 1e-5 of the largest entry.
 
     In the blurred-noise cell the void elements (filtered density below 0.01, moduli near
     1e-9) carry 3e-8 of the sensitivity norm, and their displacements are only weakly fixed
     by a residual criterion: solved against FP32 coupling blocks their sensitivities differ
-    from the FP64 oracle's by ~1e-2 of their own size whatever the tolerance (measured on
-    the oracle's own solution fed to the element kernel: 2e-7; on the GPU's solution: 1e-6
-    overall, all of it in the void). The 1e-6 bar therefore applies to the elements with
-    density >= 0.01, and the void ones are bounded against the vector's scale."""
+    from the FP64 oracle's by ~1e-2 of their own size whatever the tolerance (the element
+    kernel on the oracle's own displacements: 2e-7 overall). They enter the L2 bar with
+    the rest but are not bounded one by one."""
     mod, gold = _golden64()
+    import os
     n = gold["n"]
     cell = gold["cells"][kind]
     assert max(cell["relres"]) <= 1e-11
+    full = np.load(os.path.join(os.path.dirname(__file__), "golden", "oracle_64_sens.npz"))
     rho_t = mod.filtered_density(kind, n)
     hom = make(B, n)
     hom.set_density(cuda(rho_t))
@@ -270,19 +271,17 @@ def test_CH_and_sensitivities_match_stored_oracle_64(B, kind):
     Cref = np.array(cell["C"])
     close(C, Cref, 1e-6)
     idx = mod.sample_indices(n)
+    solid = rho_t >= 0.01
     for objective in ("bulk", "shear"):
         _, g = oracle.objective(objective, Cref)
         s = torch.empty(n ** 3, device="cuda")
         hom.sensitivity(g, s)
         got = host(s)
-        want = cell["sensitivity"][objective]
-        ref = np.array(want["sample"])
-        solid = rho_t[idx] >= 0.01
-        assert rel(got[idx][solid], ref[solid]) < 1e-6
-        assert np.abs(got[idx] - ref).max() <= 1e-5 * np.abs(ref).max()
-        assert np.linalg.norm(got[idx][~solid] - ref[~solid]) <= 1e-6 * np.linalg.norm(ref)
-        assert abs(np.linalg.norm(got) / want["norm2"] - 1) < 1e-6
-        assert abs(got.sum() - want["sum"]) <= 1e-6 * abs(want["sum"])
+        ref = full[f"{kind}_{objective}"].astype(np.float64)
+        assert np.allclose(ref[idx], cell["sensitivity"][objective]["sample"], rtol=2e-7, atol=0)
+        assert rel(got, ref) < 1e-6, rel(got, ref)
+        assert np.abs(got[solid] - ref[solid]).max() <= 1e-5 * np.abs(ref).max()
+        assert abs(got.sum() - cell["sensitivity"][objective]["sum"]) <= 1e-6 * abs(cell["sensitivity"][objective]["sum"])
 
 
 def test_displacements_match_oracle_in_energy_norm(B):
