@@ -94,14 +94,24 @@ __global__ void __launch_bounds__(128) k_fine_true_residual(const __grid_constan
     const Nb nb = make_nb(x, y, z, n);
     float Et[8];
     load_E8(E, nb, Et);
-    float hi[kPlanes], lo[kPlanes], own[kPlanes], ownlo[kPlanes];
+    // The 6 cases advance in pairs (2p, 2p + 1) on the two lanes of f32x2 registers. Every
+    // lane performs exactly the scalar operations of the double-float recurrence below,
+    // in the same order (the negated-operand forms are exact: round to nearest is
+    // symmetric), so the result is bitwise that of a scalar evaluation:
+    //   dh + e = u_(v+d) - u_v (two-sum), dl = e + (ulo_(v+d) - ulo_v),
+    //   p = a dh, pe = a dh - p (FMA), hi + e' = hi + p (two-sum),
+    //   lo += e' + (a dl + pe).
+    f32x2 hi[9], lo[9], nown[9], ownlo[9];
 #pragma unroll
-    for (int q = 0; q < kPlanes; ++q) {
-      hi[q] = 0.f;
-      lo[q] = 0.f;
-      own[q] = __ldg(u + q * N + v);
-      ownlo[q] = __ldg(ulo + q * N + v);
-    }
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int q0 = 6 * p + k, q1 = q0 + 3;
+        hi[3 * p + k] = 0ull;
+        lo[3 * p + k] = 0ull;
+        nown[3 * p + k] = pack2(-__ldg(u + q0 * N + v), -__ldg(u + q1 * N + v));
+        ownlo[3 * p + k] = pack2(__ldg(ulo + q0 * N + v), __ldg(ulo + q1 * N + v));
+      }
 #pragma unroll 1
     for (int d = 0; d < 27; ++d) {
       if (d == 13) continue;
@@ -110,37 +120,57 @@ __global__ void __launch_bounds__(128) k_fine_true_residual(const __grid_constan
       // runtime d: the block is rebuilt with runtime offsets (same FP32 operations and
       // order as the compile-time version in the CG product)
       nb_block(K, Et, dx, dy, dz, A);
+      f32x2 Ap[9], An[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        Ap[e] = pack2(A[e], A[e]);
+        An[e] = pack2(-A[e], -A[e]);
+      }
       const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
 #pragma unroll
-      for (int c = 0; c < kCases; ++c) {
-        float dh[3], dl[3];
+      for (int p = 0; p < 3; ++p) {
+        f32x2 dh[3], dl[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          const size_t o = static_cast<size_t>(3 * c + k) * N + w;
-          float e;
-          two_sum(__ldg(u + o), -own[3 * c + k], dh[k], e);
-          dl[k] = __fadd_rn(e, __fadd_rn(__ldg(ulo + o), -ownlo[3 * c + k]));
+          const size_t o0 = static_cast<size_t>(6 * p + k) * N + w, o1 = o0 + 3 * N;
+          const f32x2 a = pack2(__ldg(u + o0), __ldg(u + o1));
+          const f32x2 b = nown[3 * p + k];
+          const f32x2 s = fadd2(a, b);                      // two-sum of u_(v+d) and -u_v
+          const f32x2 bb = fsub2(s, a);
+          const f32x2 e = fadd2(fsub2(a, fsub2(s, bb)), fsub2(b, bb));
+          dh[k] = s;
+          dl[k] = fadd2(e, fsub2(pack2(__ldg(ulo + o0), __ldg(ulo + o1)), ownlo[3 * p + k]));
         }
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            const float a = A[3 * r + k];
-            const float p = __fmul_rn(a, dh[k]);
-            const float pe = fmaf(a, dh[k], -p);
-            float s, e;
-            two_sum(hi[3 * c + r], p, s, e);
-            hi[3 * c + r] = s;
-            lo[3 * c + r] = __fadd_rn(lo[3 * c + r], __fadd_rn(e, fmaf(a, dl[k], pe)));
+            const f32x2 pr = fmul2(Ap[3 * r + k], dh[k]);
+            const f32x2 npe = ffma2(An[3 * r + k], dh[k], pr);      // = -(a dh - p) exactly
+            const f32x2 h = hi[3 * p + r];
+            const f32x2 s = fadd2(h, pr);                            // two-sum of hi and p
+            const f32x2 bb = fsub2(s, h);
+            const f32x2 e = fadd2(fsub2(h, fsub2(s, bb)), fsub2(pr, bb));
+            hi[3 * p + r] = s;
+            // e + (a dl + pe) = e - (-a dl - pe) = e - fma(-a, dl, -pe)
+            lo[3 * p + r] = fadd2(lo[3 * p + r], fsub2(e, ffma2(An[3 * r + k], dl[k], npe)));
           }
       }
     }
+    float hs[kPlanes], ls[kPlanes];
+#pragma unroll
+    for (int p = 0; p < 3; ++p)
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        unpack2(hi[3 * p + r], hs[6 * p + r], hs[6 * p + 3 + r]);
+        unpack2(lo[3 * p + r], ls[6 * p + r], ls[6 * p + 3 + r]);
+      }
 #pragma unroll
     for (int q = 0; q < kPlanes; ++q) {
       const size_t o = static_cast<size_t>(q) * N + v;
       float s, e;
-      two_sum(__ldg(b + o), -hi[q], s, e);
-      const float val = __fadd_rn(s, __fadd_rn(e, __fadd_rn(__ldg(blo + o), -lo[q])));
+      two_sum(__ldg(b + o), -hs[q], s, e);
+      const float val = __fadd_rn(s, __fadd_rn(e, __fadd_rn(__ldg(blo + o), -ls[q])));
       out[o] = val;
       red[q / 3] = fmaf(val, val, red[q / 3]);
       red[kCases + q] += val;
