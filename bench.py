@@ -74,6 +74,9 @@ def parse_args(argv=None):
     ap.add_argument("--warm-start", default="previous", choices=["previous", "learned", "delta"],
                     help="start of each solve: the previous iterate (default), the warm-start network's "
                          "prediction, or the previous iterate plus the predicted change since it")
+    ap.add_argument("--compare-starts", action="store_true",
+                    help="also replay the timed steps with the learned start (network trained in the setup) "
+                         "and report both starts side by side")
     ap.add_argument("--train-n", type=int, default=64, help="cell size of the network's training snapshots")
     ap.add_argument("--train-cells", type=int, default=3)
     ap.add_argument("--train-iters", type=int, default=8, help="optimisation iterations per training cell")
@@ -678,9 +681,13 @@ def run_ours(args, rank, world, local):
         tuning = {"cases_per_thread": choice[0], "threads_per_block": choice[1],
                   "ms_per_sweep": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times.items()}}
     net_info = None
-    if args.warm_start != "previous":
+    compare = None
+    if args.warm_start != "previous" or args.compare_starts:
         net, s_u, net_info = train_warm_start(args, dev, stream)
-        loop.learned = LearnedStart(args, hom, net, s_u, dev)
+        if args.warm_start != "previous":
+            loop.learned = LearnedStart(args, hom, net, s_u, dev)
+        else:
+            compare = LearnedStart(argparse.Namespace(**{**vars(args), "warm_start": "learned"}), hom, net, s_u, dev)
 
     # warm-up (the first one is the cold solve from zero displacement)
     cold_ms = None
@@ -742,6 +749,20 @@ def run_ours(args, rank, world, local):
     hom.profile(False)
     prof_same = [list(c) for c in loop.cg] == cg_timed[:prof_steps]
 
+    # the same steps from the same snapshot with the learned start (timed the same way)
+    starts = None
+    if compare is not None:
+        loop.restore(snap)
+        loop.learned = compare
+        t_l = timed_steps(loop, args.steps, world, dev)
+        starts = {"previous": {"ms_per_step": ms_step, "cg_iterations_per_step": [max(c) for c in cg_timed]},
+                  "learned": {"ms_per_step": t_l / args.steps,
+                              "cg_iterations_per_step": [max(c) for c in loop.cg],
+                              "max_final_relres": max(loop.relres)},
+                  "note": "both replay the timed steps from the same snapshot; the learned start's time "
+                          "includes pooling, the forward pass and the prolongation"}
+        loop.learned = None
+
     second = None
     if args.second_n and args.second_n != n and world == 1:
         del snap
@@ -796,6 +817,8 @@ def run_ours(args, rank, world, local):
         line["second_size"] = second
     if net_info is not None:
         line["warm_start"] = dict(mode=args.warm_start, **net_info)
+    if starts is not None:
+        line["start_comparison"] = starts
     if tuning is not None:
         line["autotune"] = tuning
     print(json.dumps(line), flush=True)
