@@ -19,6 +19,12 @@ namespace {
 
 // Error-free transformations (Knuth TwoSum, FMA-based TwoProduct) with operations the
 // compiler may not contract or reorder.
+__device__ __forceinline__ f32x2 fmul2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fadd_rn(s, -a);
