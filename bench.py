@@ -51,7 +51,9 @@ def parse_args(argv=None):
     ap.add_argument("--profile-steps", type=int, default=5,
                     help="steps of the separate per-launch-timed replay that gives the kernel breakdown")
     ap.add_argument("--sweeps", type=int, default=0,
-                    help="smoothing sweeps before/after coarse correction (0 = library default, 1)")
+                    help="finest-level smoothing sweeps before/after coarse correction (0 = library default, 1)")
+    ap.add_argument("--coarse-sweeps", type=int, default=0,
+                    help="sweeps before/after coarse correction on the coarser levels (0 = library default, 3)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
     ap.add_argument("--sym", default="none", choices=["none", "reflect3", "rotate3", "reflect6"],
                     help="symmetry enforced on the sensitivity and the density every step")
@@ -348,9 +350,11 @@ def config_dict(args):
                           if args.precision == "fp32" else
                           "FP32 arithmetic; coarse-level stencils stored in BF16 (symmetrised); "
                           "double-float displacement and CG correction"),
-            "smoother": (f"8-colour block Gauss-Seidel, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle"
+            "smoother": (f"8-colour block Gauss-Seidel, {args.sweeps or 1}+{args.sweeps or 1} sweeps on the finest "
+                         f"level and {args.coarse_sweeps or 3}+{args.coarse_sweeps or 3} on the coarser ones per V-cycle"
                          if args.smoother == "gs8" else
-                         f"Chebyshev(2)/block-Jacobi, {args.sweeps or 1}+{args.sweeps or 1} sweeps per V-cycle")}
+                         f"Chebyshev(2)/block-Jacobi, {args.sweeps or 1}+{args.sweeps or 1} sweeps on the finest level "
+                         f"and {args.coarse_sweeps or 3}+{args.coarse_sweeps or 3} on the coarser ones per V-cycle")}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -564,7 +568,8 @@ class Loop:
         from synthetic import smoothed_threshold_density
         self.b, self.args, self.n, self.stream, self.dev = binding, args, n, stream, dev
         self.hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream,
-                                          smoother=args.smoother, precision=args.precision)
+                                          smoother=args.smoother, precision=args.precision,
+                                          coarse_sweeps=args.coarse_sweeps)
         self.r = torch.from_numpy(smoothed_threshold_density(n, args.vf, seed)).to(dev)
         self.rt = torch.empty_like(self.r)
         self.s = torch.empty_like(self.r)
@@ -868,7 +873,8 @@ def run_batch(args, rank, world, local):
     cells = []
     for n, vf, obj, seed in specs:
         st = torch.cuda.Stream()
-        hom = binding.Homogenization(n, stream=st.cuda_stream, graphs=args.graphs, precision=args.precision)
+        hom = binding.Homogenization(n, stream=st.cuda_stream, graphs=args.graphs, precision=args.precision,
+                                     coarse_sweeps=args.coarse_sweeps)
         r = torch.from_numpy(smoothed_threshold_density(n, vf, seed)).cuda()
         cells.append({"hom": hom, "stream": st, "n": n, "vf": vf, "obj": obj, "r": r,
                       "rt": torch.empty_like(r), "s": torch.empty_like(r), "dc": torch.empty_like(r)})

@@ -82,6 +82,11 @@ typedef struct homo_opts {
   int precision;    /* HOMO_PRECISION_FP32 (default) or HOMO_PRECISION_MIXED             */
   int graphs;       /* 1: replay each CG iteration as a captured CUDA graph (needs a
                        non-NULL stream; not while profiling), 0 (default): plain launches */
+  int coarse_sweeps; /* smoothing sweeps before and after the coarse correction on every
+                       level below the finest (0 = default 3; the finest level keeps
+                       pre_sweeps / post_sweeps). The paper does not state its sweep
+                       counts; coarse sweeps cost 1/8 per level of a fine one and cut the
+                       CG iterations, which the finest level dominates. */
 } homo_opts;
 
 /* Smoothers. GS8: 8-colour block Gauss-Seidel (Sec. 4.1-4.2, Eq. 15-16), colours 0..7
