@@ -53,7 +53,9 @@ def parse_args(argv=None):
     ap.add_argument("--sweeps", type=int, default=0,
                     help="finest-level smoothing sweeps before/after coarse correction (0 = library default, 1)")
     ap.add_argument("--coarse-sweeps", type=int, default=0,
-                    help="sweeps before/after coarse correction on the coarser levels (0 = library default, 3)")
+                    help="sweeps before/after coarse correction on level 1 (0 = library default, 1)")
+    ap.add_argument("--sweep-growth", type=int, default=0,
+                    help="factor by which each further level's sweeps grow, capped at 64 (0 = library default, 3)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
     ap.add_argument("--sym", default="none", choices=["none", "reflect3", "rotate3", "reflect6"],
                     help="symmetry enforced on the sensitivity and the density every step")
@@ -350,11 +352,11 @@ def config_dict(args):
                           if args.precision == "fp32" else
                           "FP32 arithmetic; coarse-level stencils stored in BF16 (symmetrised); "
                           "double-float displacement and CG correction"),
-            "smoother": (f"8-colour block Gauss-Seidel, {args.sweeps or 1}+{args.sweeps or 1} sweeps on the finest "
-                         f"level and {args.coarse_sweeps or 3}+{args.coarse_sweeps or 3} on the coarser ones per V-cycle"
-                         if args.smoother == "gs8" else
-                         f"Chebyshev(2)/block-Jacobi, {args.sweeps or 1}+{args.sweeps or 1} sweeps on the finest level "
-                         f"and {args.coarse_sweeps or 3}+{args.coarse_sweeps or 3} on the coarser ones per V-cycle")}
+            "smoother": ("8-colour block Gauss-Seidel" if args.smoother == "gs8" else "Chebyshev(2)/block-Jacobi")
+                        + f", sweeps before+after the coarse correction: {args.sweeps or 1}+{args.sweeps or 1} on the "
+                          f"finest level, {args.coarse_sweeps or 1}+{args.coarse_sweeps or 1} on level 1, growing "
+                          f"{args.sweep_growth or 3}x per further level (at most 64)",
+            "graphs": bool(args.graphs)}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -569,7 +571,8 @@ class Loop:
         self.b, self.args, self.n, self.stream, self.dev = binding, args, n, stream, dev
         self.hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream,
                                           smoother=args.smoother, precision=args.precision,
-                                          coarse_sweeps=args.coarse_sweeps)
+                                          coarse_sweeps=args.coarse_sweeps, sweep_growth=args.sweep_growth,
+                                          graphs=args.graphs)
         self.r = torch.from_numpy(smoothed_threshold_density(n, args.vf, seed)).to(dev)
         self.rt = torch.empty_like(self.r)
         self.s = torch.empty_like(self.r)
@@ -874,7 +877,7 @@ def run_batch(args, rank, world, local):
     for n, vf, obj, seed in specs:
         st = torch.cuda.Stream()
         hom = binding.Homogenization(n, stream=st.cuda_stream, graphs=args.graphs, precision=args.precision,
-                                     coarse_sweeps=args.coarse_sweeps)
+                                     coarse_sweeps=args.coarse_sweeps, sweep_growth=args.sweep_growth)
         r = torch.from_numpy(smoothed_threshold_density(n, vf, seed)).cuda()
         cells.append({"hom": hom, "stream": st, "n": n, "vf": vf, "obj": obj, "r": r,
                       "rt": torch.empty_like(r), "s": torch.empty_like(r), "dc": torch.empty_like(r)})

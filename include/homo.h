@@ -82,12 +82,18 @@ typedef struct homo_opts {
   int precision;    /* HOMO_PRECISION_FP32 (default) or HOMO_PRECISION_MIXED             */
   int graphs;       /* 1: replay each CG iteration as a captured CUDA graph (needs a
                        non-NULL stream; not while profiling), 0 (default): plain launches */
-  int coarse_sweeps; /* smoothing sweeps before and after the coarse correction on every
-                       level below the finest (0 = default 3; the finest level keeps
-                       pre_sweeps / post_sweeps). The paper does not state its sweep
-                       counts; coarse sweeps cost 1/8 per level of a fine one and cut the
-                       CG iterations, which the finest level dominates. */
+  int coarse_sweeps; /* smoothing sweeps before and after the coarse correction on level 1,
+                       the first level below the finest (0 = default 1)                   */
+  int sweep_growth;  /* each further level smooths this many times as often as the level
+                       above it, at most HOMO_MAX_LEVEL_SWEEPS (0 = default 3: 1, 3, 9,
+                       27, 64, ... sweeps on levels 1, 2, 3, ...). The paper does not state
+                       its sweep counts; a sweep costs 1/8 per level of one on the level
+                       above, and the deeper smoothing cuts the CG iterations, whose cost
+                       the finest level dominates (the finest level keeps pre_sweeps /
+                       post_sweeps). */
 } homo_opts;
+
+#define HOMO_MAX_LEVEL_SWEEPS 64
 
 /* Smoothers. GS8: 8-colour block Gauss-Seidel (Sec. 4.1-4.2, Eq. 15-16), colours 0..7
  * before and 7..0 after the coarse correction. CHEBYSHEV: Chebyshev polynomial in

@@ -28,7 +28,7 @@ class HomoOpts(ctypes.Structure):
                 ("max_levels", ctypes.c_int), ("pre_sweeps", ctypes.c_int),
                 ("post_sweeps", ctypes.c_int), ("smoother", ctypes.c_int),
                 ("cheb_degree", ctypes.c_int), ("precision", ctypes.c_int), ("graphs", ctypes.c_int),
-                ("coarse_sweeps", ctypes.c_int)]
+                ("coarse_sweeps", ctypes.c_int), ("sweep_growth", ctypes.c_int)]
 
 
 SMOOTHERS = {"gs8": 0, "chebyshev": 1}
@@ -209,11 +209,11 @@ class Homogenization:
     def __init__(self, n: int, E0: float = 1.0, nu: float = 0.3, p: float = 3.0, Emin: float = 1e-9,
                  min_coarse: int = 0, max_levels: int = 0, sweeps: int = 0, stream=None,
                  smoother: str = "gs8", cheb_degree: int = 0, precision: str = "fp32",
-                 graphs: bool = False, coarse_sweeps: int = 0):
+                 graphs: bool = False, coarse_sweeps: int = 0, sweep_growth: int = 0):
         self.lib = load_library()
         opts = HomoOpts(ctypes.sizeof(HomoOpts), min_coarse, max_levels, sweeps, sweeps,
                         SMOOTHERS[smoother], cheb_degree, PRECISIONS[precision], int(graphs),
-                        coarse_sweeps)
+                        coarse_sweeps, sweep_growth)
         h = _vp()
         st = self.lib.homo_create(ctypes.byref(h), n, E0, nu, p, Emin, ctypes.byref(opts))
         if st != HOMO_OK:

@@ -228,6 +228,13 @@ int smooth_level(homo_ctx* c, int l, bool reverse, const float* f, float* x, boo
   return HOMO_OK;
 }
 
+// Smoothing sweeps before (and after) the coarse correction on coarse level l >= 1.
+int level_sweeps(const homo_ctx* c, int l) {
+  int s = c->opts.coarse_sweeps;
+  for (int k = 1; k < l; ++k) s = std::min(HOMO_MAX_LEVEL_SWEEPS, s * c->opts.sweep_growth);
+  return s;
+}
+
 // Chebyshev iteration coefficients on [lam/10, lam] (three-term recurrence): step 0
 // x1 = x0 + (1/theta) D^-1 r0; step k >= 1 x_(k+1) = x_k + ca_k (x_k - x_(k-1)) + cb_k D^-1 r_k.
 struct ChebCoef {
@@ -283,7 +290,7 @@ int cheb_sweep(homo_ctx* c, int l, const float* b, const double* bmean, float*& 
 // correction, so M is symmetric); two buffers per level alternate as iterates.
 int vcycle_cheb(homo_ctx* c, const float* r, float* z, const double* rmean) {
   cudaStream_t s = c->stream;
-  const int pre = c->opts.pre_sweeps, post = c->opts.post_sweeps, cs = c->opts.coarse_sweeps;
+  const int pre = c->opts.pre_sweeps, post = c->opts.post_sweeps;
   const int L = c->nlev - 1;
   float* cur[kMaxLevels];
   float* oth[kMaxLevels];
@@ -296,7 +303,7 @@ int vcycle_cheb(homo_ctx* c, const float* r, float* z, const double* rmean) {
     Level& lv = c->lev[l];
     cur[l] = lv.x;
     oth[l] = lv.t;
-    for (int k = 0; k < cs; ++k) RET(cheb_sweep(c, l, lv.b, nullptr, cur[l], oth[l], k == 0));
+    for (int k = 0; k < level_sweeps(c, l); ++k) RET(cheb_sweep(c, l, lv.b, nullptr, cur[l], oth[l], k == 0));
     KL(c, HOMO_KC_COARSE_RESIDUAL, 1, launch_coarse_residual(lv, lv.b, cur[l], oth[l], s));
     KL(c, HOMO_KC_TRANSFER, 1, launch_restrict(lv.n, oth[l], c->lev[l + 1].b, s));
   }
@@ -305,7 +312,7 @@ int vcycle_cheb(homo_ctx* c, const float* r, float* z, const double* rmean) {
   for (int l = L - 1; l >= 1; --l) {
     Level& lv = c->lev[l];
     KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(lv.n, cur[l + 1], cur[l], 0, s));
-    for (int k = 0; k < cs; ++k) RET(cheb_sweep(c, l, lv.b, nullptr, cur[l], oth[l], false));
+    for (int k = 0; k < level_sweeps(c, l); ++k) RET(cheb_sweep(c, l, lv.b, nullptr, cur[l], oth[l], false));
   }
   KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(c->n, cur[1], cur[0], 0, s));
   for (int k = 0; k < post; ++k) RET(cheb_sweep(c, 0, r, rmean, cur[0], oth[0], false));
@@ -325,7 +332,7 @@ int vcycle(homo_ctx* c, const float* r, float* z, const double* rmean = nullptr)
     return HOMO_OK;
   }
   if (c->opts.smoother == HOMO_SMOOTH_CHEBYSHEV) return vcycle_cheb(c, r, z, rmean);
-  const int pre = c->opts.pre_sweeps, post = c->opts.post_sweeps, cs = c->opts.coarse_sweeps;
+  const int pre = c->opts.pre_sweeps, post = c->opts.post_sweeps;
   if (pre == 0) CK(c, cudaMemsetAsync(z, 0, sizeof(float) * kPlanes * c->N, s));
   for (int k = 0; k < pre; ++k) RET(smooth_level(c, 0, false, r, z, k == 0, rmean));
   KL(c, HOMO_KC_FINE_RESIDUAL, 1, launch_fine_residual(c, r, z, nullptr, c->q, nullptr, nullptr, rmean));
@@ -333,6 +340,7 @@ int vcycle(homo_ctx* c, const float* r, float* z, const double* rmean = nullptr)
   const int L = c->nlev - 1;
   for (int l = 1; l < L; ++l) {
     Level& lv = c->lev[l];
+    const int cs = level_sweeps(c, l);
     for (int k = 0; k < cs; ++k) RET(smooth_level(c, l, false, lv.b, lv.x, k == 0));
     KL(c, HOMO_KC_COARSE_RESIDUAL, 1, launch_coarse_residual(lv, lv.b, lv.x, lv.t, s));
     KL(c, HOMO_KC_TRANSFER, 1, launch_restrict(lv.n, lv.t, c->lev[l + 1].b, s));
@@ -341,6 +349,7 @@ int vcycle(homo_ctx* c, const float* r, float* z, const double* rmean = nullptr)
   for (int l = L - 1; l >= 1; --l) {
     Level& lv = c->lev[l];
     KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(lv.n, c->lev[l + 1].x, lv.x, 0, s));
+    const int cs = level_sweeps(c, l);
     for (int k = 0; k < cs; ++k) RET(smooth_level(c, l, true, lv.b, lv.x));
   }
   KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(c->n, c->lev[1].x, z, 0, s));
@@ -771,7 +780,8 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
   o.cheb_degree = 2;
   o.precision = HOMO_PRECISION_FP32;
   o.graphs = 0;
-  o.coarse_sweeps = 3;
+  o.coarse_sweeps = 1;
+  o.sweep_growth = 3;
   if (opts) {
     if (opts->struct_size != static_cast<int>(sizeof(homo_opts)))
       return set_err(nullptr, HOMO_EINVAL, "homo_opts.struct_size mismatch");
@@ -784,15 +794,17 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
     o.precision = opts->precision;
     o.graphs = opts->graphs;
     if (opts->coarse_sweeps) o.coarse_sweeps = opts->coarse_sweeps;
+    if (opts->sweep_growth) o.sweep_growth = opts->sweep_growth;
   }
   if (o.min_coarse < 3 || o.max_levels < 0 || o.max_levels > kMaxLevels || o.pre_sweeps < 0 ||
       o.post_sweeps < 0 || o.pre_sweeps > 16 || o.post_sweeps > 16 || o.pre_sweeps != o.post_sweeps ||
       (o.smoother != HOMO_SMOOTH_GS8 && o.smoother != HOMO_SMOOTH_CHEBYSHEV) || o.cheb_degree < 2 ||
       o.cheb_degree > 4 || (o.precision != HOMO_PRECISION_FP32 && o.precision != HOMO_PRECISION_MIXED) ||
-      (o.graphs != 0 && o.graphs != 1) || o.coarse_sweeps < 1 || o.coarse_sweeps > 16)
+      (o.graphs != 0 && o.graphs != 1) || o.coarse_sweeps < 1 || o.coarse_sweeps > HOMO_MAX_LEVEL_SWEEPS ||
+      o.sweep_growth < 1 || o.sweep_growth > 8)
     return set_err(nullptr, HOMO_EINVAL,
                    "bad homo_opts (min_coarse >= 3, pre == post sweeps <= 16, smoother 0/1, degree 2..4, "
-                   "precision 0/1, graphs 0/1, coarse sweeps 1..16)");
+                   "precision 0/1, graphs 0/1, coarse sweeps 1..64, sweep growth 1..8)");
   int sizes[kMaxLevels];
   int nlev = 1;
   sizes[0] = n;
