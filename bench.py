@@ -54,6 +54,8 @@ def parse_args(argv=None):
                     help="finest-level smoothing sweeps before/after coarse correction (0 = library default, 1)")
     ap.add_argument("--coarse-sweeps", type=int, default=0,
                     help="sweeps before/after coarse correction on level 1 (0 = library default, 1)")
+    ap.add_argument("--min-coarse", type=int, default=0,
+                    help="coarsen while the next level keeps at least this many cells per axis (0 = library default, 4)")
     ap.add_argument("--sweep-growth", type=int, default=0,
                     help="factor by which each further level's sweeps grow, capped at 64 (0 = library default, 3)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
@@ -572,6 +574,7 @@ class Loop:
         self.hom = binding.Homogenization(n, sweeps=args.sweeps, stream=stream.cuda_stream,
                                           smoother=args.smoother, precision=args.precision,
                                           coarse_sweeps=args.coarse_sweeps, sweep_growth=args.sweep_growth,
+                                          min_coarse=args.min_coarse,
                                           graphs=args.graphs)
         self.r = torch.from_numpy(smoothed_threshold_density(n, args.vf, seed)).to(dev)
         self.rt = torch.empty_like(self.r)
