@@ -712,6 +712,9 @@ def run_ours(args, rank, world, local):
             cold_ms = e0.elapsed_time(e1)
     snap = loop.snapshot()
     loop.restore(snap)
+    # kernels launched before the timed region (the probe's 16, the library's and the
+    # snapshot's copy): the skip count of an ncu launch list of the timed steps
+    launches_before = 16 + loop.launches() + 1
 
     # timed region: device time of K steps, no per-launch instrumentation
     sampler = ClockSampler(local)
@@ -816,7 +819,7 @@ def run_ours(args, rank, world, local):
         "dtype": "f32", "data": "synthetic", "config": config_dict(args),
         "roofline": roofline, "stencil": stencil, "fp32_peak": fp32_peak,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-        "gpu_launches": launches,
+        "gpu_launches": launches, "launches_before_timed": launches_before,
         "solver": {"cold_first_iteration_ms": cold_ms,
                    "cg_iterations_per_step": cg.max(axis=1).tolist() if cg.size else [],
                    "max_final_relres": max(relres_timed) if relres_timed else None},
