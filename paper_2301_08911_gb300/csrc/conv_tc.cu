@@ -356,8 +356,8 @@ cudaError_t tc_launch(int n, const void* x, const void* w, const float* bias, co
 
 }  // namespace
 
-// tcgen05 convolution for c_in in {16, 32} and every epilogue (same contract as the
-// shared-memory-staged mma.sync path it replaces).
+// tcgen05 convolution for c_in in {16, 32} and every epilogue (the contract of
+// homo_nn_conv3d).
 cudaError_t conv3d_tc(int n, int cin, int epi, const void* x, const void* w, const float* bias, const void* res,
                       const void* mask, void* out, float* outf, const double* scale, cudaStream_t s) {
 #define HOMO_TC_CASE(CI, EP) \
