@@ -58,6 +58,10 @@ def parse_args(argv=None):
                     help="coarsen while the next level keeps at least this many cells per axis (0 = library default, 4)")
     ap.add_argument("--sweep-growth", type=int, default=0,
                     help="factor by which each further level's sweeps grow, capped at 64 (0 = library default, 3)")
+    ap.add_argument("--coarse-smoother", type=int, nargs=2, default=None, metavar=("CLUSTER_MAX_N", "SPLIT_MAX_N"),
+                    help="coarse Gauss-Seidel kernels: levels of at most CLUSTER_MAX_N cells per axis smooth as "
+                         "one cluster launch per phase, at most SPLIT_MAX_N with a thread per (vertex, case) "
+                         "(default: the library's)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
     ap.add_argument("--sym", default="none", choices=["none", "reflect3", "rotate3", "reflect6"],
                     help="symmetry enforced on the sensitivity and the density every step")
@@ -576,6 +580,8 @@ class Loop:
                                           coarse_sweeps=args.coarse_sweeps, sweep_growth=args.sweep_growth,
                                           min_coarse=args.min_coarse,
                                           graphs=args.graphs)
+        if args.coarse_smoother:
+            self.hom.set_coarse_smoother(*args.coarse_smoother)
         self.r = torch.from_numpy(smoothed_threshold_density(n, args.vf, seed)).to(dev)
         self.rt = torch.empty_like(self.r)
         self.s = torch.empty_like(self.r)
@@ -822,7 +828,9 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches, "launches_before_timed": launches_before,
         "solver": {"cold_first_iteration_ms": cold_ms,
                    "cg_iterations_per_step": cg.max(axis=1).tolist() if cg.size else [],
-                   "max_final_relres": max(relres_timed) if relres_timed else None},
+                   "max_final_relres": max(relres_timed) if relres_timed else None,
+                   "coarse_smoother": dict(zip(("cluster_max_n", "split_max_n", "cluster"),
+                                               hom.coarse_smoother()))},
         "kernels": {"steps": prof_steps, "replays_timed_steps": prof_same,
                     "note": "separate replay of the first timed steps with CUDA events around every launch",
                     **{k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}},
@@ -884,6 +892,8 @@ def run_batch(args, rank, world, local):
         st = torch.cuda.Stream()
         hom = binding.Homogenization(n, stream=st.cuda_stream, graphs=args.graphs, precision=args.precision,
                                      coarse_sweeps=args.coarse_sweeps, sweep_growth=args.sweep_growth)
+        if args.coarse_smoother:
+            hom.set_coarse_smoother(*args.coarse_smoother)
         r = torch.from_numpy(smoothed_threshold_density(n, vf, seed)).cuda()
         cells.append({"hom": hom, "stream": st, "n": n, "vf": vf, "obj": obj, "r": r,
                       "rt": torch.empty_like(r), "s": torch.empty_like(r), "dc": torch.empty_like(r)})

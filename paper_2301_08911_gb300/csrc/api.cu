@@ -223,8 +223,27 @@ int smooth_level(homo_ctx* c, int l, bool reverse, const float* f, float* x, boo
   for (int k = 0; k < 8; ++k) {
     const int col = reverse ? 7 - k : k;
     if (l == 0) KL(c, HOMO_KC_FINE_GS, 1, launch_fine_gs(c, col, f, x, fz, fmean));
+    else if (c->lev[l].n <= c->gs_split_n)
+      KL(c, HOMO_KC_COARSE_GS, 1, launch_coarse_gs_item(c->lev[l], col, f, x, fz, c->stream));
     else KL(c, HOMO_KC_COARSE_GS, 1, launch_coarse_gs(c->lev[l], col, f, x, fz, c->stream));
   }
+  return HOMO_OK;
+}
+
+// sweeps 8-colour sweeps on level l; first: the first sweep starts from x = 0. A coarse
+// level with at most gs_fuse_n cells per axis runs them all as one cluster launch (the
+// per-colour launches of those levels are mostly launch latency), otherwise one launch
+// per colour.
+int smooth_level_sweeps(homo_ctx* c, int l, bool reverse, const float* f, float* x, int sweeps,
+                        bool first = false) {
+  if (sweeps < 1) return HOMO_OK;
+  if (l >= 1 && c->gs_cluster > 0 && c->lev[l].n <= c->gs_fuse_n) {
+    KL(c, HOMO_KC_COARSE_GS, 1,
+       launch_coarse_gs_sweeps(c->lev[l], sweeps, reverse ? 1 : 0, first && !reverse ? 1 : 0, f, x,
+                               c->gs_cluster, c->stream));
+    return HOMO_OK;
+  }
+  for (int k = 0; k < sweeps; ++k) RET(smooth_level(c, l, reverse, f, x, first && k == 0));
   return HOMO_OK;
 }
 
@@ -340,8 +359,7 @@ int vcycle(homo_ctx* c, const float* r, float* z, const double* rmean = nullptr)
   const int L = c->nlev - 1;
   for (int l = 1; l < L; ++l) {
     Level& lv = c->lev[l];
-    const int cs = level_sweeps(c, l);
-    for (int k = 0; k < cs; ++k) RET(smooth_level(c, l, false, lv.b, lv.x, k == 0));
+    RET(smooth_level_sweeps(c, l, false, lv.b, lv.x, level_sweeps(c, l), true));
     KL(c, HOMO_KC_COARSE_RESIDUAL, 1, launch_coarse_residual(lv, lv.b, lv.x, lv.t, s));
     KL(c, HOMO_KC_TRANSFER, 1, launch_restrict(lv.n, lv.t, c->lev[l + 1].b, s));
   }
@@ -349,8 +367,7 @@ int vcycle(homo_ctx* c, const float* r, float* z, const double* rmean = nullptr)
   for (int l = L - 1; l >= 1; --l) {
     Level& lv = c->lev[l];
     KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(lv.n, c->lev[l + 1].x, lv.x, 0, s));
-    const int cs = level_sweeps(c, l);
-    for (int k = 0; k < cs; ++k) RET(smooth_level(c, l, true, lv.b, lv.x));
+    RET(smooth_level_sweeps(c, l, true, lv.b, lv.x, level_sweeps(c, l)));
   }
   KL(c, HOMO_KC_TRANSFER, 1, launch_prolong_add(c->n, c->lev[1].x, z, 0, s));
   for (int k = 0; k < post; ++k) RET(smooth_level(c, 0, true, r, z, false, rmean));
@@ -825,6 +842,7 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
   c->N = static_cast<size_t>(n) * n * n;
   c->E0 = E0; c->nu = nu; c->p = p; c->Emin = Emin;
   c->opts = o;
+  c->gs_cluster = coarse_cluster_size();
   c->opts.struct_size = sizeof(homo_opts);
   build_element_matrix(nu, c->ke, c->ld, c->chi);
   c->hBf.assign(8 * 576, 0.f);
@@ -1309,7 +1327,25 @@ int homo_smooth(homo_ctx* ctx, int level, int reverse, const float* f, float* u)
   if (!ctx || !f || !u || level < 0 || level >= ctx->nlev) return HOMO_EINVAL;
   if (ctx->lev[level].n % 2 != 0) return set_err(ctx, HOMO_EINVAL, "smoothing needs an even level size");
   RET(ensure_hierarchy(ctx));
-  return smooth_level(ctx, level, reverse != 0, f, u);
+  return smooth_level_sweeps(ctx, level, reverse != 0, f, u, 1);
+}
+
+int homo_set_coarse_smoother(homo_ctx* ctx, int cluster_max_n, int split_max_n) {
+  if (!ctx) return HOMO_EINVAL;
+  if (cluster_max_n < 0 || cluster_max_n > 1024 || split_max_n < 0 || split_max_n > 1024)
+    return set_err(ctx, HOMO_EINVAL, "coarse smoother sizes must be in [0, 1024]");
+  if (cluster_max_n != ctx->gs_fuse_n || split_max_n != ctx->gs_split_n) drop_graphs(ctx);
+  ctx->gs_fuse_n = cluster_max_n;
+  ctx->gs_split_n = split_max_n;
+  return HOMO_OK;
+}
+
+int homo_coarse_smoother(const homo_ctx* ctx, int* cluster_max_n, int* split_max_n, int* cluster) {
+  if (!ctx) return HOMO_EINVAL;
+  if (cluster_max_n) *cluster_max_n = ctx->gs_fuse_n;
+  if (split_max_n) *split_max_n = ctx->gs_split_n;
+  if (cluster) *cluster = ctx->gs_cluster;
+  return HOMO_OK;
 }
 
 int homo_vcycle(homo_ctx* ctx, const float* r, float* z) {

@@ -3,6 +3,9 @@
 // solve with the rigid-translation null space projected out.
 #include "dev_common.cuh"
 
+#include <algorithm>
+#include <mutex>
+
 namespace homo {
 
 namespace {
@@ -160,25 +163,42 @@ __global__ void __launch_bounds__(256) k_stencil_bf16(const float* __restrict__ 
   }
 }
 
-__device__ __forceinline__ void solve3x6c(const float (&S)[9], float (&b)[18]) {
+// LDL^T factors of the symmetric 3x3 diagonal block S_v (Eq. 16): multipliers l10, l20,
+// l21 and the reciprocal pivots i0, i1, i2.
+struct Factor3 {
+  float l10, l20, l21, i0, i1, i2;
+};
+
+__device__ __forceinline__ Factor3 factor3(const float (&S)[9]) {
+  Factor3 F;
   const float d0 = S[0];
-  const float l10 = S[3] / d0, l20 = S[6] / d0;
-  const float d1 = S[4] - l10 * S[1];
-  const float l21 = (S[7] - l20 * S[1]) / d1;
-  const float d2 = S[8] - l20 * S[2] - l21 * (S[5] - l10 * S[2]);
-  const float i0 = 1.f / d0, i1 = 1.f / d1, i2 = 1.f / d2;
+  F.l10 = S[3] / d0;
+  F.l20 = S[6] / d0;
+  const float d1 = S[4] - F.l10 * S[1];
+  F.l21 = (S[7] - F.l20 * S[1]) / d1;
+  const float d2 = S[8] - F.l20 * S[2] - F.l21 * (S[5] - F.l10 * S[2]);
+  F.i0 = 1.f / d0;
+  F.i1 = 1.f / d1;
+  F.i2 = 1.f / d2;
+  return F;
+}
+
+// Solve S_v x = (y0, y1, y2) in place for one load case.
+__device__ __forceinline__ void solve3(const Factor3& F, float& y0, float& y1, float& y2) {
+  y1 -= F.l10 * y0;
+  y2 -= F.l20 * y0 + F.l21 * y1;
+  const float x2 = y2 * F.i2;
+  const float x1 = y1 * F.i1 - F.l21 * x2;
+  const float x0 = y0 * F.i0 - F.l10 * x1 - F.l20 * x2;
+  y0 = x0;
+  y1 = x1;
+  y2 = x2;
+}
+
+__device__ __forceinline__ void solve3x6c(const float (&S)[9], float (&b)[18]) {
+  const Factor3 F = factor3(S);
 #pragma unroll
-  for (int c = 0; c < kCases; ++c) {
-    float y0 = b[3 * c], y1 = b[3 * c + 1], y2 = b[3 * c + 2];
-    y1 -= l10 * y0;
-    y2 -= l20 * y0 + l21 * y1;
-    const float x2 = y2 * i2;
-    const float x1 = y1 * i1 - l21 * x2;
-    const float x0 = y0 * i0 - l10 * x1 - l20 * x2;
-    b[3 * c] = x0;
-    b[3 * c + 1] = x1;
-    b[3 * c + 2] = x2;
-  }
+  for (int c = 0; c < kCases; ++c) solve3(F, b[3 * c], b[3 * c + 1], b[3 * c + 2]);
 }
 
 // One colour pass of block Gauss-Seidel (Eq. 15-16) with the stored stencil. Neighbours
@@ -230,6 +250,154 @@ __global__ void __launch_bounds__(256) k_coarse_gs(const T* __restrict__ st,
     solve3x6c(S, rhs);
 #pragma unroll
     for (int q = 0; q < kPlanes; ++q) x[q * N + v] = rhs[q];
+  }
+}
+
+// One load case of one vertex of a block Gauss-Seidel colour pass (Eq. 15-16): exactly
+// the arithmetic of that case in k_coarse_gs (the same FMAs in the same order, the same
+// factorisation and solve), so it produces bitwise the same value. The 26 neighbours are
+// visited in three z-layers of 9 (d = 0..8, 9..17, 18..26, the order of the FMA chain);
+// the 108 stencil and displacement values of a layer are loaded before its FMAs, so a
+// thread waits for three rounds of loads instead of one per neighbour (the small coarse
+// levels are bound by that latency). COHERENT: x is read through L2 only, for kernels in
+// which other CTAs write x between colour passes; otherwise through the read-only path
+// (a pass reads only vertices of other colours, which it does not write).
+template <typename T, bool COHERENT>
+__device__ __forceinline__ void gs_item(const T* __restrict__ st, const float* __restrict__ f, float* x,
+                                        int n, size_t N, unsigned Nh, int h, int colour, int fz, int c,
+                                        unsigned m) {
+  const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
+  int i, j, kk;
+  decode3(m, static_cast<unsigned>(h), i, j, kk);
+  const int X = 2 * i + cx, Y = 2 * j + cy, Z = 2 * kk + cz;
+  const size_t p = static_cast<size_t>(colour) * Nh + m;
+  const size_t v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
+  const Nb nb = make_nb(X, Y, Z, n);
+  const float* fc = f + static_cast<size_t>(3 * c) * N;
+  const float* xc = x + static_cast<size_t>(3 * c) * N;
+  float b0 = __ldg(fc + v), b1 = __ldg(fc + N + v), b2 = __ldg(fc + 2 * N + v);
+  float S[9];
+#pragma unroll
+  for (int layer = 0; layer < 3; ++layer) {
+    float A[9][9], U[9][3];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const int d = 9 * layer + e;
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const int odd = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+      if (d == 13) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) S[q] = ld_st(st + static_cast<size_t>(9 * 13 + q) * N + p);
+        continue;
+      }
+      if (fz && (colour ^ odd) > colour) continue;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) A[e][q] = ld_st(st + static_cast<size_t>(9 * d + q) * N + p);
+      const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+      if (COHERENT) {
+        U[e][0] = __ldcg(xc + w);
+        U[e][1] = __ldcg(xc + N + w);
+        U[e][2] = __ldcg(xc + 2 * N + w);
+      } else {
+        U[e][0] = __ldg(xc + w);
+        U[e][1] = __ldg(xc + N + w);
+        U[e][2] = __ldg(xc + 2 * N + w);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const int d = 9 * layer + e;
+      const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+      const int odd = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+      if (d == 13 || (fz && (colour ^ odd) > colour)) continue;
+      const float u0 = U[e][0], u1 = U[e][1], u2 = U[e][2];
+      b0 = fmaf(-A[e][2], u2, fmaf(-A[e][1], u1, fmaf(-A[e][0], u0, b0)));
+      b1 = fmaf(-A[e][5], u2, fmaf(-A[e][4], u1, fmaf(-A[e][3], u0, b1)));
+      b2 = fmaf(-A[e][8], u2, fmaf(-A[e][7], u1, fmaf(-A[e][6], u0, b2)));
+    }
+  }
+  solve3(factor3(S), b0, b1, b2);
+  float* xo = x + static_cast<size_t>(3 * c) * N + v;
+  if (COHERENT) {
+    __stcg(xo, b0);
+    __stcg(xo + N, b1);
+    __stcg(xo + 2 * N, b2);
+  } else {
+    xo[0] = b0;
+    xo[N] = b1;
+    xo[2 * N] = b2;
+  }
+}
+
+// Work items of a colour pass: one warp per (32 consecutive vertices of the colour, load
+// case), the six case warps of a vertex block adjacent, so that a 192-thread CTA covers
+// all six cases of its 32 vertices (their stencil rows are shared through L1) and every
+// warp's loads are coalesced along the vertex index. Returns false for the padding lanes
+// beyond the last vertex.
+constexpr int kItemBlock = 192;
+
+__device__ __forceinline__ bool gs_item_index(unsigned it, unsigned Nh, int& c, unsigned& m) {
+  const unsigned g = it >> 5;
+  const unsigned mb = g / kCases;
+  c = static_cast<int>(g - mb * kCases);
+  m = mb * 32 + (it & 31);
+  return m < Nh;
+}
+
+__host__ __device__ inline unsigned gs_items(unsigned Nh) { return (Nh + 31) / 32 * 32 * kCases; }
+
+// One colour pass with a thread per (load case, vertex of the colour): six times the
+// threads of k_coarse_gs, each with a sixth of its FMAs and its loads in flight a z-layer
+// at a time.
+template <typename T>
+__global__ void __launch_bounds__(kItemBlock) k_coarse_gs_item(const T* __restrict__ st,
+                                                               const float* __restrict__ f, float* x,
+                                                               int n, int colour, int first) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  const int h = n >> 1;
+  const unsigned Nh = static_cast<unsigned>(h) * h * h;
+  const unsigned items = gs_items(Nh);
+  for (unsigned it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+    int c;
+    unsigned m;
+    if (gs_item_index(it, Nh, c, m)) gs_item<T, false>(st, f, x, n, N, Nh, h, colour, first, c, m);
+  }
+}
+
+// Every sweep of one smoothing phase on a small level in one launch. Gauss-Seidel does
+// not couple the load cases, so the grid is six thread-block clusters of csize CTAs, one
+// per case, that never wait on one another: a cluster's colour passes are separated by
+// its own hardware barrier (release at arrival, acquire at the wait, cluster scope), so a
+// pass sees every value the passes before it wrote; x is read and written through L2.
+// Spreading the cases over six clusters puts six times as many SMs on the small levels,
+// whose passes are bound by load latency and load issue. Items as in k_coarse_gs_item
+// (gs_item per vertex and case), so the iterates are bitwise those of the per-colour
+// launches. sweeps >= 1; reverse: colours 7..0; first: the first sweep starts from x = 0
+// (forward order only, as in k_coarse_gs).
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+constexpr int kClusterBlock = 64;
+
+template <typename T>
+__global__ void __launch_bounds__(kClusterBlock) k_coarse_gs_cluster(const T* __restrict__ st,
+                                                                     const float* __restrict__ f,
+                                                                     float* x, int n, int sweeps,
+                                                                     int reverse, int first, int csize) {
+  const size_t N = static_cast<size_t>(n) * n * n;
+  const int h = n >> 1;
+  const unsigned Nh = static_cast<unsigned>(h) * h * h;
+  const int c = static_cast<int>(blockIdx.x) / csize;   // load case of this cluster
+  const unsigned nthreads = static_cast<unsigned>(csize) * blockDim.x;
+  const unsigned tid = (blockIdx.x - static_cast<unsigned>(c * csize)) * blockDim.x + threadIdx.x;
+  for (int s = 0; s < sweeps; ++s) {
+    const int fz = first && s == 0 && !reverse ? 1 : 0;
+    for (int k = 0; k < 8; ++k) {
+      const int colour = reverse ? 7 - k : k;
+      for (unsigned m = tid; m < Nh; m += nthreads) gs_item<T, true>(st, f, x, n, N, Nh, h, colour, fz, c, m);
+      cluster_barrier();
+    }
   }
 }
 
@@ -582,6 +750,90 @@ cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* 
   const size_t h = static_cast<size_t>(L.n / 2);
   if (L.sth) k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.sth, f, x, L.n, colour, first);
   else k_coarse_gs<<<grid_for(h * h * h, 256), 256, 0, s>>>(L.st, f, x, L.n, colour, first);
+  return cudaGetLastError();
+}
+
+namespace {
+
+template <typename T>
+int cluster_fits(int size) {
+  const void* fn = reinterpret_cast<const void*>(k_coarse_gs_cluster<T>);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, size > 8 ? 1 : 0) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(size);
+  cfg.blockDim = dim3(kClusterBlock);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int count = 0;
+  if (cudaOccupancyMaxActiveClusters(&count, fn, &cfg) != cudaSuccess) return 0;
+  return count;
+}
+
+std::mutex g_cluster_mu;
+int g_cluster_size[256] = {};   // per device: 0 = not queried, -1 = no cluster launch
+
+}  // namespace
+
+int coarse_cluster_size() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lk(g_cluster_mu);
+  if (g_cluster_size[dev] == 0) {
+    int best = -1;
+    for (int size : {16, 8, 4}) {
+      if (cluster_fits<float>(size) > 0 && cluster_fits<__nv_bfloat16>(size) > 0) {
+        best = size;
+        break;
+      }
+    }
+    cudaGetLastError();   // a refused size leaves its error behind
+    g_cluster_size[dev] = best;
+  }
+  return g_cluster_size[dev];
+}
+
+cudaError_t launch_coarse_gs_sweeps(const Level& L, int sweeps, int reverse, int first, const float* f,
+                                    float* x, int cluster_max, cudaStream_t s) {
+  const unsigned h = static_cast<unsigned>(L.n / 2);
+  const size_t Nh = static_cast<size_t>(h) * h * h;
+  // per case: the smallest power-of-two cluster with a thread per vertex of a colour, at
+  // most cluster_max CTAs
+  const size_t need = (Nh + kClusterBlock - 1) / kClusterBlock;
+  int size = 1;
+  while (size < cluster_max && static_cast<size_t>(size) < need) size *= 2;
+  if (size > cluster_max) size = cluster_max;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCases * size);
+  cfg.blockDim = dim3(kClusterBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (L.sth)
+    return cudaLaunchKernelEx(&cfg, k_coarse_gs_cluster<__nv_bfloat16>, L.sth, f, x, L.n, sweeps, reverse, first, size);
+  return cudaLaunchKernelEx(&cfg, k_coarse_gs_cluster<float>, L.st, f, x, L.n, sweeps, reverse, first, size);
+}
+
+cudaError_t launch_coarse_gs_item(const Level& L, int colour, const float* f, float* x, int first,
+                                  cudaStream_t s) {
+  const unsigned h = static_cast<unsigned>(L.n / 2);
+  const int g = grid_for(gs_items(h * h * h), kItemBlock);
+  if (L.sth) k_coarse_gs_item<<<g, kItemBlock, 0, s>>>(L.sth, f, x, L.n, colour, first);
+  else k_coarse_gs_item<<<g, kItemBlock, 0, s>>>(L.st, f, x, L.n, colour, first);
   return cudaGetLastError();
 }
 

@@ -172,6 +172,12 @@ struct homo_ctx {
   // fine Gauss-Seidel variant: load cases per thread (3 or 6) and threads per block
   // (128 or 256); set by homo_set_tuning / homo_autotune
   int gs_cases = 3, gs_block = 256;
+  // coarse Gauss-Seidel kernels (homo_set_coarse_smoother): levels with at most gs_fuse_n
+  // cells per axis run every sweep of a smoothing phase as one thread-block-cluster launch,
+  // levels with at most gs_split_n one launch per colour with a thread per (vertex, case),
+  // larger levels one launch per colour with a thread per vertex; gs_cluster: the largest
+  // cluster the device launches (-1: none, per-colour launches everywhere)
+  int gs_fuse_n = 16, gs_split_n = 32, gs_cluster = -1;
 
   cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};
   long long cg_graph_launches[2] = {0, 0};   // kernels per replay
@@ -251,6 +257,17 @@ cudaError_t launch_coarse_residual(const Level& L, const float* b, const float* 
                                    cudaStream_t s);
 cudaError_t launch_coarse_gs(const Level& L, int colour, const float* f, float* x, int first,
                              cudaStream_t s);
+// Every sweep of one smoothing phase of level L (sweeps 8-colour sweeps, colours 7..0 when
+// reverse, the first from x = 0 when first) as one launch of a thread-block cluster of at
+// most cluster_max CTAs; bitwise the iterates of the per-colour launches.
+cudaError_t launch_coarse_gs_sweeps(const Level& L, int sweeps, int reverse, int first, const float* f,
+                                    float* x, int cluster_max, cudaStream_t s);
+// One colour pass of level L with a thread per (vertex, case); bitwise launch_coarse_gs.
+cudaError_t launch_coarse_gs_item(const Level& L, int colour, const float* f, float* x, int first,
+                                  cudaStream_t s);
+// Largest cluster (16, 8 or 4 CTAs) the fused smoother can launch on the current device,
+// -1 when none; queried once per device.
+int coarse_cluster_size();
 cudaError_t launch_restrict(int nf, const float* fine, float* coarse, cudaStream_t s);
 cudaError_t launch_prolong_add(int nf, const float* coarse, float* fine, int overwrite,
                                cudaStream_t s);

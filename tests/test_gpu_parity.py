@@ -133,16 +133,24 @@ def test_restrict_and_prolong_match_oracle(B):
     close(host(xf).reshape(18, -1), ref, 1e-6)
 
 
-@pytest.mark.parametrize("level,reverse", [(0, False), (0, True), (1, False)])
-def test_gauss_seidel_sweep_matches_oracle(B, level, reverse):
-    n = 8
+# kernels: the coarse Gauss-Seidel form of every coarse level (the finest level has one)
+_COARSE_FORMS = {"cluster": (1024, 0), "item": (0, 1024), "vertex": (0, 0)}
+
+
+@pytest.mark.parametrize("n,level,reverse,form", [(8, 0, False, "cluster"), (8, 0, True, "cluster"),
+                                                  (8, 1, False, "cluster"), (8, 1, False, "item"),
+                                                  (8, 1, False, "vertex"), (16, 1, True, "cluster"),
+                                                  (16, 1, True, "item"), (16, 1, False, "vertex"),
+                                                  (16, 2, False, "cluster")])
+def test_gauss_seidel_sweep_matches_oracle(B, n, level, reverse, form):
     rho = uniform_density(n, 500, 0.05, 1.0)
-    hom = make(B, n, min_coarse=3)      # levels 8, 4
+    hom = make(B, n, min_coarse=3)      # levels 8, 4 or 16, 8, 4
+    hom.set_coarse_smoother(*_COARSE_FORMS[form])
     hom.set_density(cuda(rho))
     h = 1.0 / n
     K = oracle.assemble_K(n, oracle.simp_modulus(rho), oracle.ke_hex8(1, 0.3, h)) / h
-    if level == 1:
-        K = oracle.galerkin(K, n // 2)
+    for lv in range(level):
+        K = oracle.galerkin(K, n >> (lv + 1))
     nl = n >> level
     f = mean_free(uniform_field(18 * nl ** 3, 501, -1, 1).reshape(18, -1).astype(np.float64))
     u0 = uniform_field(18 * nl ** 3, 502, -1, 1).reshape(18, -1).astype(np.float64)
