@@ -58,10 +58,12 @@ def parse_args(argv=None):
                     help="coarsen while the next level keeps at least this many cells per axis (0 = library default, 4)")
     ap.add_argument("--sweep-growth", type=int, default=0,
                     help="factor by which each further level's sweeps grow, capped at 64 (0 = library default, 3)")
-    ap.add_argument("--coarse-smoother", type=int, nargs=2, default=None, metavar=("CLUSTER_MAX_N", "SPLIT_MAX_N"),
-                    help="coarse Gauss-Seidel kernels: levels of at most CLUSTER_MAX_N cells per axis smooth as "
-                         "one cluster launch per phase, at most SPLIT_MAX_N with a thread per (vertex, case) "
-                         "(default: the library's)")
+    ap.add_argument("--coarse-smoother", type=int, nargs=3, default=None,
+                    metavar=("RESIDENT_MAX_N", "CLUSTER_MAX_N", "SPLIT_MAX_N"),
+                    help="coarse Gauss-Seidel kernels: levels of at most RESIDENT_MAX_N cells per axis smooth as "
+                         "one cluster launch per phase with the displacement in shared memory, at most "
+                         "CLUSTER_MAX_N as one cluster launch through L2, at most SPLIT_MAX_N with a thread per "
+                         "(vertex, case) (default: the library's)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
     ap.add_argument("--sym", default="none", choices=["none", "reflect3", "rotate3", "reflect6"],
                     help="symmetry enforced on the sensitivity and the density every step")
@@ -829,8 +831,8 @@ def run_ours(args, rank, world, local):
         "solver": {"cold_first_iteration_ms": cold_ms,
                    "cg_iterations_per_step": cg.max(axis=1).tolist() if cg.size else [],
                    "max_final_relres": max(relres_timed) if relres_timed else None,
-                   "coarse_smoother": dict(zip(("cluster_max_n", "split_max_n", "cluster"),
-                                               hom.coarse_smoother()))},
+                   "coarse_smoother": dict(zip(("resident_max_n", "cluster_max_n", "split_max_n", "cluster",
+                                                "resident_cluster"), hom.coarse_smoother()))},
         "kernels": {"steps": prof_steps, "replays_timed_steps": prof_same,
                     "note": "separate replay of the first timed steps with CUDA events around every launch",
                     **{k: {"launches": v[0], "ms": round(v[1], 3)} for k, v in prof.items() if v[0]}},

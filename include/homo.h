@@ -380,12 +380,18 @@ int homo_prolong_add(homo_ctx* ctx, int level, const float* coarse, float* fine)
 int homo_set_tuning(homo_ctx* ctx, int gs_cases, int gs_block);
 int homo_autotune(homo_ctx* ctx, int flags, int* gs_cases, int* gs_block, double* ms);
 
-/* Coarse-level Gauss-Seidel kernels (Eq. 15-16 on levels >= 1). All three forms compute
+/* Coarse-level Gauss-Seidel kernels (Eq. 15-16 on levels >= 1). All four forms compute
  * bitwise the same iterates; they differ in how the work reaches the GPU:
- *  - levels with at most cluster_max_n cells per axis: every sweep of one smoothing phase
- *    (the pre- or post-smoothing sweeps of a V-cycle, or the single sweep of homo_smooth)
- *    is one launch of six thread-block clusters of up to 16 CTAs, one per load case, each
- *    separating its colour passes by its own hardware barrier (default 16);
+ *  - levels with at most resident_max_n cells per axis (FP32 stencils, and only where the
+ *    shared memory suffices: up to 16^3 with 16-CTA clusters): every sweep of one
+ *    smoothing phase (the pre- or post-smoothing sweeps of a V-cycle, or the single sweep
+ *    of homo_smooth) is one launch of six thread-block clusters, one per load case. Each
+ *    CTA holds a copy of its case's displacement in shared memory, writes the updates of
+ *    its own vertices into every copy of the cluster, and streams the stencil rows of its
+ *    vertices for the next colour while the current one computes; the colour passes are
+ *    separated by the cluster's hardware barrier (default 16);
+ *  - other levels with at most cluster_max_n cells per axis: the same per-case cluster
+ *    launch, reading the displacement and stencils through L2 (default 16);
  *  - larger levels with at most split_max_n cells per axis: one launch per colour pass with
  *    a thread per (vertex, load case), each loading a z-layer of 9 neighbours before its
  *    FMAs (default 32);
@@ -393,13 +399,14 @@ int homo_autotune(homo_ctx* ctx, int flags, int* gs_cases, int* gs_block, double
  * The small levels are bound by load latency and launch overhead, not by bytes: with the
  * default sweep counts a V-cycle of a 512^3 cell runs about 2,500 colour passes on levels
  * of 32^3 and below. Sizes in [0, 1024]; 0 disables a form. Changing them drops the
- * context's captured CUDA graphs. Where the device cannot launch a cluster of at least 4
- * CTAs of 64 threads, the per-colour forms are used whatever cluster_max_n says.
- * homo_coarse_smoother reports the sizes and the cluster size in use (-1: none); outputs
- * nullable. Both return HOMO_EINVAL for a NULL context or sizes out of range. (The paper
- * launches one kernel per colour pass; this setting has no counterpart there.) */
-int homo_set_coarse_smoother(homo_ctx* ctx, int cluster_max_n, int split_max_n);
-int homo_coarse_smoother(const homo_ctx* ctx, int* cluster_max_n, int* split_max_n, int* cluster);
+ * context's captured CUDA graphs. Where the device cannot launch the clusters, the next
+ * form applies whatever the sizes say. homo_coarse_smoother reports the sizes and the
+ * largest cluster of the L2 and of the resident form the device launches (-1: none);
+ * outputs nullable. Both return HOMO_EINVAL for a NULL context or sizes out of range.
+ * (The paper launches one kernel per colour pass; this setting has no counterpart there.) */
+int homo_set_coarse_smoother(homo_ctx* ctx, int resident_max_n, int cluster_max_n, int split_max_n);
+int homo_coarse_smoother(const homo_ctx* ctx, int* resident_max_n, int* cluster_max_n, int* split_max_n,
+                         int* cluster, int* resident_cluster);
 
 /* One 8-colour block Gauss-Seidel sweep (Eq. 15-16) on level l, in place on u, colours
  * 0..7 (reverse = 0) or 7..0 (reverse = 1). f, u: device, 6-case layout on level l. */

@@ -108,8 +108,8 @@ SIGNATURES = {
     "homo_prolong_add": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp]),
     "homo_set_tuning": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
     "homo_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_int_p, _c_double_p]),
-    "homo_set_coarse_smoother": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int]),
-    "homo_coarse_smoother": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p]),
+    "homo_set_coarse_smoother": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "homo_coarse_smoother": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p]),
     "homo_net_train_step": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_double_p, ctypes.c_double,
                                            _c_double_p]),
     "homo_net_release": (ctypes.c_int, [_vp]),
@@ -351,17 +351,21 @@ class Homogenization:
     def set_tuning(self, gs_cases: int, gs_block: int):
         self._check(self.lib.homo_set_tuning(self.h, gs_cases, gs_block))
 
-    def set_coarse_smoother(self, cluster_max_n: int, split_max_n: int):
-        """Coarse Gauss-Seidel kernels by level size: at most cluster_max_n cells per axis
-        smooth as one cluster launch per phase, at most split_max_n with a thread per
-        (vertex, case) per colour, larger levels with a thread per vertex (0 disables)."""
-        self._check(self.lib.homo_set_coarse_smoother(self.h, int(cluster_max_n), int(split_max_n)))
+    def set_coarse_smoother(self, resident_max_n: int, cluster_max_n: int, split_max_n: int):
+        """Coarse Gauss-Seidel kernels by level size: at most resident_max_n cells per axis
+        smooth as one cluster launch per phase with the displacement in shared memory, at
+        most cluster_max_n as one cluster launch through L2, at most split_max_n with a
+        thread per (vertex, case) per colour, larger levels with a thread per vertex
+        (0 disables a form)."""
+        self._check(self.lib.homo_set_coarse_smoother(self.h, int(resident_max_n), int(cluster_max_n),
+                                                      int(split_max_n)))
 
     def coarse_smoother(self):
-        """(cluster_max_n, split_max_n, cluster size in use or -1)."""
-        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        self._check(self.lib.homo_coarse_smoother(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
-        return a.value, b.value, c.value
+        """(resident_max_n, cluster_max_n, split_max_n, cluster size, resident cluster size),
+        the cluster sizes -1 where the device launches none."""
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(self.lib.homo_coarse_smoother(self.h, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
 
     def autotune(self, retime: bool = False):
         """Time the fine Gauss-Seidel variants on this cell, select the fastest. Returns

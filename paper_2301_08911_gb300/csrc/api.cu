@@ -230,13 +230,20 @@ int smooth_level(homo_ctx* c, int l, bool reverse, const float* f, float* x, boo
   return HOMO_OK;
 }
 
-// sweeps 8-colour sweeps on level l; first: the first sweep starts from x = 0. A coarse
-// level with at most gs_fuse_n cells per axis runs them all as one cluster launch (the
-// per-colour launches of those levels are mostly launch latency), otherwise one launch
-// per colour.
+// sweeps 8-colour sweeps on level l; first: the first sweep starts from x = 0. A small
+// coarse level runs them all as one launch of per-case clusters (its displacement resident
+// in shared memory up to gs_res_n cells per axis, read through L2 up to gs_fuse_n), larger
+// levels one launch per colour (the per-colour launches of the small levels are mostly
+// launch and load latency).
 int smooth_level_sweeps(homo_ctx* c, int l, bool reverse, const float* f, float* x, int sweeps,
                         bool first = false) {
   if (sweeps < 1) return HOMO_OK;
+  if (l >= 1 && c->gs_resident > 0 && c->lev[l].n <= c->gs_res_n && coarse_resident_ok(c->lev[l], c->gs_resident)) {
+    KL(c, HOMO_KC_COARSE_GS, 1,
+       launch_coarse_gs_resident(c->lev[l], sweeps, reverse ? 1 : 0, first && !reverse ? 1 : 0, f, x,
+                                 c->gs_resident, c->stream));
+    return HOMO_OK;
+  }
   if (l >= 1 && c->gs_cluster > 0 && c->lev[l].n <= c->gs_fuse_n) {
     KL(c, HOMO_KC_COARSE_GS, 1,
        launch_coarse_gs_sweeps(c->lev[l], sweeps, reverse ? 1 : 0, first && !reverse ? 1 : 0, f, x,
@@ -843,6 +850,7 @@ int homo_create(homo_ctx** out, int n, double E0, double nu, double p, double Em
   c->E0 = E0; c->nu = nu; c->p = p; c->Emin = Emin;
   c->opts = o;
   c->gs_cluster = coarse_cluster_size();
+  c->gs_resident = coarse_resident_size();
   c->opts.struct_size = sizeof(homo_opts);
   build_element_matrix(nu, c->ke, c->ld, c->chi);
   c->hBf.assign(8 * 576, 0.f);
@@ -1330,20 +1338,26 @@ int homo_smooth(homo_ctx* ctx, int level, int reverse, const float* f, float* u)
   return smooth_level_sweeps(ctx, level, reverse != 0, f, u, 1);
 }
 
-int homo_set_coarse_smoother(homo_ctx* ctx, int cluster_max_n, int split_max_n) {
+int homo_set_coarse_smoother(homo_ctx* ctx, int resident_max_n, int cluster_max_n, int split_max_n) {
   if (!ctx) return HOMO_EINVAL;
-  if (cluster_max_n < 0 || cluster_max_n > 1024 || split_max_n < 0 || split_max_n > 1024)
+  if (resident_max_n < 0 || resident_max_n > 1024 || cluster_max_n < 0 || cluster_max_n > 1024 ||
+      split_max_n < 0 || split_max_n > 1024)
     return set_err(ctx, HOMO_EINVAL, "coarse smoother sizes must be in [0, 1024]");
-  if (cluster_max_n != ctx->gs_fuse_n || split_max_n != ctx->gs_split_n) drop_graphs(ctx);
+  if (resident_max_n != ctx->gs_res_n || cluster_max_n != ctx->gs_fuse_n || split_max_n != ctx->gs_split_n)
+    drop_graphs(ctx);
+  ctx->gs_res_n = resident_max_n;
   ctx->gs_fuse_n = cluster_max_n;
   ctx->gs_split_n = split_max_n;
   return HOMO_OK;
 }
 
-int homo_coarse_smoother(const homo_ctx* ctx, int* cluster_max_n, int* split_max_n, int* cluster) {
+int homo_coarse_smoother(const homo_ctx* ctx, int* resident_max_n, int* cluster_max_n, int* split_max_n,
+                         int* cluster, int* resident_cluster) {
   if (!ctx) return HOMO_EINVAL;
+  if (resident_max_n) *resident_max_n = ctx->gs_res_n;
   if (cluster_max_n) *cluster_max_n = ctx->gs_fuse_n;
   if (split_max_n) *split_max_n = ctx->gs_split_n;
+  if (resident_cluster) *resident_cluster = ctx->gs_resident;
   if (cluster) *cluster = ctx->gs_cluster;
   return HOMO_OK;
 }

@@ -401,6 +401,187 @@ __global__ void __launch_bounds__(kClusterBlock) k_coarse_gs_cluster(const T* __
   }
 }
 
+// ---- shared-memory-resident form of the small-level smoother
+// Six clusters again, one per load case; the CTAs of a cluster split each colour's
+// vertices into ranges of at most kResVerts (CTA r owns positions [r Mper, (r+1) Mper) of
+// every colour, three threads per vertex, one per block row). Every CTA keeps a full copy of its case's
+// displacement in shared memory, so all neighbour reads of a pass are shared-memory
+// loads; the owner of a vertex writes its new value into every CTA's copy (distributed
+// shared memory) before the cluster barrier that ends the pass. Each CTA streams the
+// stencil rows of its own vertices for the next colour pass into a second buffer with
+// asynchronous copies while the current pass computes, and keeps the right-hand side of
+// its vertices for all colours. The arithmetic per vertex is gs_item's, on the same
+// values in the same order: bitwise the iterates of the other forms.
+constexpr int kResVerts = 64;     // vertices per colour per CTA, at most
+constexpr int kResThreads = 256;  // threads per CTA: all stage, 3 x kResVerts compute (a row each)
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async_f4(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_f16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+
+// value into the same shared-memory offset of CTA `rank` of the cluster
+__device__ __forceinline__ void st_cluster_f32(const float* local, unsigned rank, float v) {
+  unsigned remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_addr(local)), "r"(rank));
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(remote), "f"(v) : "memory");
+}
+
+// Shared memory of k_coarse_gs_resident in floats: the case's displacement (3N), two
+// stencil buffers (2 x 243 x Mper) and the owned right-hand sides (8 x 3 x Mper).
+__host__ __device__ inline size_t resident_smem_floats(size_t N, int Mper) {
+  return 3 * N + 2 * static_cast<size_t>(kStencil) * Mper + 24 * static_cast<size_t>(Mper);
+}
+
+// Stage the stencil rows of positions colour*Nh + m0 .. + mcount of every plane: 16-byte
+// copies when every segment is 16-byte aligned (vec), 4-byte copies otherwise. Thread t
+// copies chunk t % per of planes t / per, t / per + blockDim / per, ... (per = chunks per
+// plane; the quotient is taken once per launch, not per copy).
+struct StageMap {
+  int per, plane0, step, chunk;   // step 0: the thread copies nothing
+};
+
+__device__ __forceinline__ StageMap stage_map(int mcount, bool vec) {
+  StageMap m;
+  m.per = vec ? (mcount >> 2) : mcount;
+  const int planes_per_pass = m.per > 0 ? static_cast<int>(blockDim.x) / m.per : 0;
+  if (planes_per_pass == 0 || static_cast<int>(threadIdx.x) >= planes_per_pass * m.per) {
+    m.plane0 = 0;
+    m.step = 0;
+    m.chunk = 0;
+    return m;
+  }
+  m.plane0 = static_cast<int>(threadIdx.x) / m.per;
+  m.chunk = static_cast<int>(threadIdx.x) - m.plane0 * m.per;
+  m.step = planes_per_pass;
+  return m;
+}
+
+__device__ __forceinline__ void stage_rows(const float* __restrict__ st, size_t N, unsigned Nh, int colour,
+                                           unsigned m0, int Mper, bool vec, const StageMap& sm_, float* buf) {
+  if (sm_.step > 0) {
+    const int j = vec ? (sm_.chunk << 2) : sm_.chunk;
+    const float* src = st + static_cast<size_t>(colour) * Nh + m0 + j + static_cast<size_t>(sm_.plane0) * N;
+    float* dst = buf + sm_.plane0 * Mper + j;
+    const size_t src_step = static_cast<size_t>(sm_.step) * N;
+    const int dst_step = sm_.step * Mper;
+    for (int plane = sm_.plane0; plane < kStencil; plane += sm_.step, src += src_step, dst += dst_step) {
+      if (vec) cp_async_f16(dst, src);
+      else cp_async_f4(dst, src);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+__global__ void __launch_bounds__(kResThreads) k_coarse_gs_resident(const float* __restrict__ st,
+                                                                  const float* __restrict__ f, float* x,
+                                                                  int n, int sweeps, int reverse, int first,
+                                                                  int csize, int Mper, int vec16) {
+  extern __shared__ float sm[];
+  const size_t N = static_cast<size_t>(n) * n * n;
+  const int h = n >> 1;
+  const unsigned Nh = static_cast<unsigned>(h) * h * h;
+  const int c = static_cast<int>(blockIdx.x) / csize;   // load case of this cluster
+  const unsigned rank = blockIdx.x - static_cast<unsigned>(c * csize);
+  const unsigned m0 = rank * static_cast<unsigned>(Mper);
+  const int mcount = m0 >= Nh ? 0 : static_cast<int>(min(static_cast<unsigned>(Mper), Nh - m0));
+  const bool vec = vec16 && (mcount % 4 == 0);   // vec16: st, N, Nh and Mper allow 16-byte segments
+  float* us = sm;                                          // [3][N]
+  float* sb[2] = {us + 3 * N, us + 3 * N + kStencil * Mper};
+  float* fs = sb[1] + kStencil * Mper;                     // [8][3][Mper]
+  const float* xc = x + static_cast<size_t>(3 * c) * N;
+  const float* fc = f + static_cast<size_t>(3 * c) * N;
+  const int r = static_cast<int>(threadIdx.x) / kResVerts;   // row of the vertex's block rows (3: stage only)
+  const int j = static_cast<int>(threadIdx.x) - r * kResVerts;
+  __shared__ float rows_s[3][kResVerts];
+
+  for (size_t i = threadIdx.x; i < 3 * N; i += blockDim.x) us[i] = __ldcg(xc + i);
+  for (int i = threadIdx.x; i < 8 * mcount; i += blockDim.x) {
+    const int colour = i / mcount, jj = i - colour * mcount;
+    int a, b, cc;
+    decode3(m0 + jj, static_cast<unsigned>(h), a, b, cc);
+    const size_t v = static_cast<size_t>(2 * a + (colour & 1)) +
+                     static_cast<size_t>(n) * ((2 * b + ((colour >> 1) & 1)) + static_cast<size_t>(n) * (2 * cc + (colour >> 2)));
+#pragma unroll
+    for (int k = 0; k < 3; ++k) fs[(colour * 3 + k) * Mper + jj] = __ldg(fc + k * N + v);
+  }
+  const int total = sweeps * 8;
+  const StageMap smap = stage_map(mcount, vec);
+  stage_rows(st, N, Nh, reverse ? 7 : 0, m0, Mper, vec, smap, sb[0]);
+  cluster_barrier();   // every copy of the displacement is loaded before any owner writes into it
+
+  for (int pass = 0; pass < total; ++pass) {
+    const int k = pass & 7;
+    const int colour = reverse ? 7 - k : k;
+    const int fz = first && pass < 8 && !reverse ? 1 : 0;
+    if (pass + 1 < total) {
+      const int kn = (pass + 1) & 7;
+      stage_rows(st, N, Nh, reverse ? 7 - kn : kn, m0, Mper, vec, smap, sb[(pass + 1) & 1]);
+    } else {
+      asm volatile("cp.async.commit_group;\n" ::: "memory");
+    }
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+    // thread (row r, vertex j): the FMA chain of row r of the vertex's three rows (the
+    // rows are independent chains); the solve gathers the three rows through rows_s
+    const int cx = colour & 1, cy = (colour >> 1) & 1, cz = colour >> 2;
+    size_t v = 0;
+    if (r < 3 && j < mcount) {
+      const float* S_ = sb[pass & 1];
+      int a, b, cc;
+      decode3(m0 + j, static_cast<unsigned>(h), a, b, cc);
+      const int X = 2 * a + cx, Y = 2 * b + cy, Z = 2 * cc + cz;
+      v = static_cast<size_t>(X) + static_cast<size_t>(n) * (Y + static_cast<size_t>(n) * Z);
+      const Nb nb = make_nb(X, Y, Z, n);
+      float br = fs[(colour * 3 + r) * Mper + j];
+#pragma unroll
+      for (int d = 0; d < 27; ++d) {
+        if (d == 13) continue;
+        const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+        const int odd = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
+        if (fz && (colour ^ odd) > colour) continue;
+        const float* Ad = S_ + (9 * d + 3 * r) * Mper + j;
+        const size_t w = static_cast<size_t>(nb.X[dx + 1] + nb.Y[dy + 1] + nb.Z[dz + 1]);
+        br = fmaf(-Ad[2 * Mper], us[2 * N + w], fmaf(-Ad[Mper], us[N + w], fmaf(-Ad[0], us[w], br)));
+      }
+      rows_s[r][j] = br;
+    }
+    __syncthreads();
+    if (r < 3 && j < mcount) {
+      const float* S_ = sb[pass & 1];
+      float S[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) S[q] = S_[(9 * 13 + q) * Mper + j];
+      float y0 = rows_s[0][j], y1 = rows_s[1][j], y2 = rows_s[2][j];
+      solve3(factor3(S), y0, y1, y2);
+      const float val = r == 0 ? y0 : (r == 1 ? y1 : y2);
+      float* dst = us + static_cast<size_t>(r) * N + v;
+      *dst = val;
+      for (unsigned t = 0; t < static_cast<unsigned>(csize); ++t)
+        if (t != rank) st_cluster_f32(dst, t, val);
+    }
+    cluster_barrier();
+  }
+  // every vertex is owned by one CTA: write the owned values back
+  for (int i = threadIdx.x; i < 8 * mcount; i += blockDim.x) {
+    const int colour = i / mcount, jj = i - colour * mcount;
+    int a, b, cc;
+    decode3(m0 + jj, static_cast<unsigned>(h), a, b, cc);
+    const size_t v = static_cast<size_t>(2 * a + (colour & 1)) +
+                     static_cast<size_t>(n) * ((2 * b + ((colour >> 1) & 1)) + static_cast<size_t>(n) * (2 * cc + (colour >> 2)));
+    float* xo = x + static_cast<size_t>(3 * c) * N + v;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) __stcg(xo + k * N, us[k * N + v]);
+  }
+}
+
 // out = b - K x with the stored stencil; threads walk stencil positions (coalesced).
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_residual(const T* __restrict__ st,
@@ -776,7 +957,45 @@ int cluster_fits(int size) {
 }
 
 std::mutex g_cluster_mu;
-int g_cluster_size[256] = {};   // per device: 0 = not queried, -1 = no cluster launch
+int g_cluster_size[256] = {};    // per device: 0 = not queried, -1 = no cluster launch
+int g_resident_size[256] = {};   // per device: largest resident-form cluster, -1 = none
+constexpr int kResidentSmemMax = 200 * 1024;   // dynamic; the static row scratch comes on top
+
+int resident_fits(int size) {
+  const void* fn = reinterpret_cast<const void*>(k_coarse_gs_resident);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, size > 8 ? 1 : 0) != cudaSuccess ||
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kResidentSmemMax) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(size);
+  cfg.blockDim = dim3(kResThreads);
+  cfg.dynamicSmemBytes = kResidentSmemMax;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = size;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int count = 0;
+  if (cudaOccupancyMaxActiveClusters(&count, fn, &cfg) != cudaSuccess) return 0;
+  return count;
+}
+
+// Cluster size and per-CTA vertex count of the resident form on level L, or false when
+// the level does not qualify (BF16 stencil, too many vertices, too much shared memory).
+bool resident_shape(const Level& L, int cluster_max, int& csize, int& Mper, size_t& smem) {
+  if (L.sth || cluster_max < 1 || L.n % 2) return false;
+  const size_t h = static_cast<size_t>(L.n / 2), Nh = h * h * h;
+  const size_t need = (Nh + kResVerts - 1) / kResVerts;
+  int size = 1;
+  while (size < cluster_max && static_cast<size_t>(size) < need) size *= 2;
+  if (static_cast<size_t>(size) < need) return false;
+  csize = size;
+  Mper = static_cast<int>((Nh + size - 1) / size);
+  smem = resident_smem_floats(L.N, Mper) * sizeof(float);
+  return smem <= static_cast<size_t>(kResidentSmemMax);
+}
 
 }  // namespace
 
@@ -795,10 +1014,59 @@ int coarse_cluster_size() {
         break;
       }
     }
+    int res = -1;
+    for (int size : {16, 8, 4, 2, 1}) {
+      if (resident_fits(size) > 0) {
+        res = size;
+        break;
+      }
+    }
     cudaGetLastError();   // a refused size leaves its error behind
     g_cluster_size[dev] = best;
+    g_resident_size[dev] = res;
   }
   return g_cluster_size[dev];
+}
+
+int coarse_resident_size() {
+  coarse_cluster_size();   // runs the per-device queries once
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    return -1;
+  }
+  std::lock_guard<std::mutex> lk(g_cluster_mu);
+  return g_resident_size[dev] == 0 ? -1 : g_resident_size[dev];
+}
+
+bool coarse_resident_ok(const Level& L, int cluster_max) {
+  int csize, Mper;
+  size_t smem;
+  return resident_shape(L, cluster_max, csize, Mper, smem);
+}
+
+cudaError_t launch_coarse_gs_resident(const Level& L, int sweeps, int reverse, int first, const float* f,
+                                      float* x, int cluster_max, cudaStream_t s) {
+  int csize, Mper;
+  size_t smem;
+  if (!resident_shape(L, cluster_max, csize, Mper, smem)) return cudaErrorInvalidValue;
+  const size_t h = static_cast<size_t>(L.n / 2), Nh = h * h * h;
+  const int vec16 = (L.N % 4 == 0) && (Nh % 4 == 0) && (Mper % 4 == 0) &&
+                    (reinterpret_cast<uintptr_t>(L.st) % 16 == 0);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kCases * csize);
+  cfg.blockDim = dim3(kResThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = csize;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_coarse_gs_resident, L.st, f, x, L.n, sweeps, reverse, first, csize, Mper,
+                            vec16);
 }
 
 cudaError_t launch_coarse_gs_sweeps(const Level& L, int sweeps, int reverse, int first, const float* f,

@@ -178,6 +178,10 @@ struct homo_ctx {
   // larger levels one launch per colour with a thread per vertex; gs_cluster: the largest
   // cluster the device launches (-1: none, per-colour launches everywhere)
   int gs_fuse_n = 16, gs_split_n = 32, gs_cluster = -1;
+  // levels with at most gs_res_n cells per axis (FP32 stencils, shared memory permitting)
+  // keep each case's displacement resident in the clusters' shared memory instead;
+  // gs_resident: the largest cluster of that form the device launches (-1: none)
+  int gs_res_n = 16, gs_resident = -1;
 
   cudaGraphExec_t cg_graph[2] = {nullptr, nullptr};
   long long cg_graph_launches[2] = {0, 0};   // kernels per replay
@@ -265,6 +269,14 @@ cudaError_t launch_coarse_gs_sweeps(const Level& L, int sweeps, int reverse, int
 // One colour pass of level L with a thread per (vertex, case); bitwise launch_coarse_gs.
 cudaError_t launch_coarse_gs_item(const Level& L, int colour, const float* f, float* x, int first,
                                   cudaStream_t s);
+// Every sweep of one smoothing phase of level L with each case's displacement resident in
+// shared memory (FP32 stencils only; coarse_resident_ok says whether L qualifies with
+// clusters of at most cluster_max CTAs); bitwise the iterates of the per-colour launches.
+cudaError_t launch_coarse_gs_resident(const Level& L, int sweeps, int reverse, int first, const float* f,
+                                      float* x, int cluster_max, cudaStream_t s);
+bool coarse_resident_ok(const Level& L, int cluster_max);
+// Largest cluster of the resident form the current device launches (-1: none).
+int coarse_resident_size();
 // Largest cluster (16, 8 or 4 CTAs) the fused smoother can launch on the current device,
 // -1 when none; queried once per device.
 int coarse_cluster_size();

@@ -121,5 +121,5 @@ def test_tuning_argument_checks(lib):
     """Host-side checks of the tuning entry points (no context, nothing launched)."""
     assert lib.homo_set_tuning(None, 3, 256) == binding.HOMO_EINVAL
     assert lib.homo_autotune(None, 0, None, None, None) == binding.HOMO_EINVAL
-    assert lib.homo_set_coarse_smoother(None, 16, 64) == binding.HOMO_EINVAL
-    assert lib.homo_coarse_smoother(None, None, None, None) == binding.HOMO_EINVAL
+    assert lib.homo_set_coarse_smoother(None, 16, 16, 32) == binding.HOMO_EINVAL
+    assert lib.homo_coarse_smoother(None, None, None, None, None, None) == binding.HOMO_EINVAL

@@ -1,10 +1,11 @@
-"""The three coarse Gauss-Seidel kernel forms (homo_set_coarse_smoother), on a GB300.
+"""The four coarse Gauss-Seidel kernel forms (homo_set_coarse_smoother), on a GB300.
 
 Per load case and vertex, every form performs the arithmetic of the thread-per-vertex
-kernel in the same order: the cluster form (every sweep of a smoothing phase in one
+kernel in the same order: the two cluster forms (every sweep of a smoothing phase in one
 launch of six clusters, one per load case, each separating its colour passes by its own
-barrier), the per-colour form with a thread per (vertex, case), and the per-colour form
-with a thread per vertex. So their iterates
+barrier; the resident one with the case's displacement in every CTA's shared memory and
+updates written into every copy, the other through L2), the per-colour form with a thread
+per (vertex, case), and the per-colour form with a thread per vertex. So their iterates
 must be bitwise equal: single sweeps in both colour orders, V-cycles (several sweeps per
 level, the first from zero), both stencil precisions, and whole solves. The oracle parity
 of each form is in test_gpu_parity.py::test_gauss_seidel_sweep_matches_oracle.
@@ -17,8 +18,9 @@ from synthetic import smoothed_threshold_density, uniform_density, uniform_field
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# (cluster_max_n, split_max_n): every coarse level in one form
-FORMS = {"vertex": (0, 0), "item": (0, 1024), "cluster": (1024, 0)}
+# (resident_max_n, cluster_max_n, split_max_n): every coarse level in one form (the
+# resident form takes the levels up to 16^3 with FP32 stencils, the L2 cluster form the rest)
+FORMS = {"vertex": (0, 0, 0), "item": (0, 0, 1024), "cluster": (0, 1024, 0), "resident": (1024, 1024, 0)}
 
 
 @pytest.fixture(scope="module")
@@ -36,22 +38,24 @@ def cuda(a):
 
 def test_settings_and_cluster_size(B):
     hom = B.Homogenization(16)
-    cluster_max_n, split_max_n, cluster = hom.coarse_smoother()
-    assert (cluster_max_n, split_max_n) == (16, 32)
+    resident_max_n, cluster_max_n, split_max_n, cluster, resident = hom.coarse_smoother()
+    assert (resident_max_n, cluster_max_n, split_max_n) == (16, 16, 32)
     assert cluster in (4, 8, 16), cluster
-    hom.set_coarse_smoother(0, 0)
-    assert hom.coarse_smoother()[:2] == (0, 0)
+    assert resident in (8, 16), resident     # 16^3 needs 8 CTAs of 64 vertices per colour
+    hom.set_coarse_smoother(0, 0, 0)
+    assert hom.coarse_smoother()[:3] == (0, 0, 0)
     with pytest.raises(B.HomoError):
-        hom.set_coarse_smoother(-1, 0)
+        hom.set_coarse_smoother(-1, 0, 0)
     with pytest.raises(B.HomoError):
-        hom.set_coarse_smoother(0, 2048)
+        hom.set_coarse_smoother(0, 0, 2048)
 
 
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 @pytest.mark.parametrize("reverse", [False, True])
 def test_single_sweeps_bitwise_equal(B, precision, reverse):
-    """n = 64: levels 32, 16, 8, 4. At 32^3 a case's cluster needs 16 CTAs with several
-    vertices per thread; at 8^3 and 4^3 it is a single CTA."""
+    """n = 64: levels 32, 16, 8, 4. At 32^3 an L2 cluster needs 16 CTAs with several
+    vertices per thread (the resident form falls back to it there); at 16^3 the resident
+    form runs 8 CTAs per case that exchange their updates, at 8^3 and 4^3 one CTA."""
     n = 64
     hom = B.Homogenization(n, precision=precision)
     hom.set_density(cuda(uniform_density(n, 900, 0.05, 1.0)))
@@ -68,7 +72,7 @@ def test_single_sweeps_bitwise_equal(B, precision, reverse):
             torch.cuda.synchronize()
             outs[form] = u
         assert not torch.equal(outs["vertex"], u0)
-        for form in ("item", "cluster"):
+        for form in ("item", "cluster", "resident"):
             assert torch.equal(outs["vertex"], outs[form]), \
                 (level, form, (outs["vertex"] - outs[form]).abs().max().item())
 
@@ -84,7 +88,8 @@ def test_vcycle_bitwise_equal(B, precision):
     r = uniform_field(18 * n ** 3, 920, -1, 1).reshape(18, -1)
     r = cuda(r - r.mean(axis=1, keepdims=True))
     outs = []
-    for sizes in [(0, 0), (0, 1024), (1024, 0), (8, 32), (16, 64), (32, 0)]:
+    for sizes in [(0, 0, 0), (0, 0, 1024), (0, 1024, 0), (1024, 1024, 0), (8, 16, 32), (16, 16, 32),
+                  (0, 32, 0), (16, 0, 64)]:
         hom.set_coarse_smoother(*sizes)
         z = torch.empty(18 * n ** 3, device="cuda")
         hom.vcycle(r, z)
@@ -98,7 +103,7 @@ def test_solve_and_CH_bitwise_equal(B):
     n = 32
     rho = cuda(smoothed_threshold_density(n, 0.3, 4))
     res = []
-    for sizes in [(0, 0), (16, 64)]:
+    for sizes in [(0, 0, 0), (16, 16, 32)]:
         hom = B.Homogenization(n)
         hom.set_coarse_smoother(*sizes)
         hom.set_density(rho)

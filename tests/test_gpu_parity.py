@@ -134,14 +134,15 @@ def test_restrict_and_prolong_match_oracle(B):
 
 
 # kernels: the coarse Gauss-Seidel form of every coarse level (the finest level has one)
-_COARSE_FORMS = {"cluster": (1024, 0), "item": (0, 1024), "vertex": (0, 0)}
+_COARSE_FORMS = {"resident": (1024, 0, 0), "cluster": (0, 1024, 0), "item": (0, 0, 1024), "vertex": (0, 0, 0)}
 
 
 @pytest.mark.parametrize("n,level,reverse,form", [(8, 0, False, "cluster"), (8, 0, True, "cluster"),
-                                                  (8, 1, False, "cluster"), (8, 1, False, "item"),
-                                                  (8, 1, False, "vertex"), (16, 1, True, "cluster"),
+                                                  (8, 1, False, "resident"), (8, 1, False, "cluster"),
+                                                  (8, 1, False, "item"), (8, 1, False, "vertex"),
+                                                  (16, 1, True, "resident"), (16, 1, True, "cluster"),
                                                   (16, 1, True, "item"), (16, 1, False, "vertex"),
-                                                  (16, 2, False, "cluster")])
+                                                  (16, 2, False, "resident"), (16, 2, False, "cluster")])
 def test_gauss_seidel_sweep_matches_oracle(B, n, level, reverse, form):
     rho = uniform_density(n, 500, 0.05, 1.0)
     hom = make(B, n, min_coarse=3)      # levels 8, 4 or 16, 8, 4
