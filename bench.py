@@ -64,6 +64,9 @@ def parse_args(argv=None):
                          "one cluster launch per phase with the displacement in shared memory, at most "
                          "CLUSTER_MAX_N as one cluster launch through L2, at most SPLIT_MAX_N with a thread per "
                          "(vertex, case) (default: the library's)")
+    ap.add_argument("--coarse-forms", action="store_true",
+                    help="after the timed region, time one Gauss-Seidel sweep of every coarse level in each kernel "
+                         "form and V-cycles under several form settings (the cell's own hierarchy)")
     ap.add_argument("--smoother", default="gs8", choices=["gs8", "chebyshev"])
     ap.add_argument("--sym", default="none", choices=["none", "reflect3", "rotate3", "reflect6"],
                     help="symmetry enforced on the sensitivity and the density every step")
@@ -365,6 +368,58 @@ def config_dict(args):
                           f"finest level, {args.coarse_sweeps or 1}+{args.coarse_sweeps or 1} on level 1, growing "
                           f"{args.sweep_growth or 3}x per further level (at most 64)",
             "graphs": bool(args.graphs)}
+
+
+# ------------------------------------------------------------------ coarse smoother forms
+def coarse_forms(hom, n, stream, dev):
+    """Device time of one 8-colour Gauss-Seidel sweep (homo_smooth) on every coarse level in
+    each kernel form, and of one V-cycle (homo_vcycle) under several form settings, on the
+    cell's own hierarchy and density; CUDA events on the context stream, 2 untimed and 20 (10
+    V-cycles) timed repetitions. Random right-hand sides and iterates of the level's size."""
+    import torch
+
+    forms = {"vertex": (0, 0, 0), "item": (0, 0, 1024), "cluster": (0, 1024, 0), "resident": (1024, 1024, 0)}
+    saved = hom.coarse_smoother()[:3]
+    gen = torch.Generator(device=dev).manual_seed(11)
+
+    def timed(fn, reps):
+        for _ in range(2):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    sweep = {}
+    level = 1
+    while level + 1 < hom.num_levels:
+        nl = n >> level
+        f = torch.rand(18 * nl ** 3, device=dev, generator=gen) - 0.5
+        u = torch.zeros_like(f)
+        row = {}
+        for name, sizes in forms.items():
+            if name in ("cluster", "resident") and nl > 32:
+                continue                       # one cluster per case: a few SMs for a large level
+            hom.set_coarse_smoother(*sizes)
+            row[name] = round(timed(lambda: hom.smooth(level, False, f, u), 20) * 1e3, 1)
+        sweep[f"{nl}^3"] = row
+        level += 1
+    r = torch.rand(18 * n ** 3, device=dev, generator=gen) - 0.5
+    r = (r.view(18, -1) - r.view(18, -1).mean(dim=1, keepdim=True)).reshape(-1).contiguous()
+    z = torch.empty_like(r)
+    vc = {}
+    for sizes in [(0, 0, 0), (0, 16, 32), tuple(saved), (8, 16, 32), (32, 32, 32)]:
+        hom.set_coarse_smoother(*sizes)
+        vc[",".join(map(str, sizes))] = round(timed(lambda: hom.vcycle(r, z), 10), 3)
+    hom.set_coarse_smoother(*saved)
+    del r, z
+    return {"sweep_us": sweep, "vcycle_ms": vc,
+            "settings": "resident_max_n,cluster_max_n,split_max_n; library default " + ",".join(map(str, saved)),
+            "note": "one homo_smooth sweep per level and form (the resident form times its shared-memory setup "
+                    "once per sweep; inside a V-cycle it runs many sweeps per launch), then homo_vcycle"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -785,6 +840,8 @@ def run_ours(args, rank, world, local):
                           "includes pooling, the forward pass and the prolongation"}
         loop.learned = None
 
+    forms = coarse_forms(hom, n, stream, dev) if args.coarse_forms else None
+
     second = None
     if args.second_n and args.second_n != n and world == 1:
         del snap
@@ -839,6 +896,8 @@ def run_ours(args, rank, world, local):
     }
     if second is not None:
         line["second_size"] = second
+    if forms is not None:
+        line["coarse_forms"] = forms
     if net_info is not None:
         line["warm_start"] = dict(mode=args.warm_start, **net_info)
     if starts is not None:
