@@ -411,7 +411,7 @@ def coarse_forms(hom, n, stream, dev):
     r = (r.view(18, -1) - r.view(18, -1).mean(dim=1, keepdim=True)).reshape(-1).contiguous()
     z = torch.empty_like(r)
     vc = {}
-    for sizes in [(0, 0, 0), (0, 16, 32), tuple(saved), (8, 16, 32), (32, 32, 32)]:
+    for sizes in [(0, 0, 0), (0, 16, 32), (16, 16, 32), tuple(saved), (8, 32, 32)]:
         hom.set_coarse_smoother(*sizes)
         vc[",".join(map(str, sizes))] = round(timed(lambda: hom.vcycle(r, z), 10), 3)
     hom.set_coarse_smoother(*saved)

@@ -391,7 +391,7 @@ int homo_autotune(homo_ctx* ctx, int flags, int* gs_cases, int* gs_block, double
  *    vertices for the next colour while the current one computes; the colour passes are
  *    separated by the cluster's hardware barrier (default 16);
  *  - other levels with at most cluster_max_n cells per axis: the same per-case cluster
- *    launch, reading the displacement and stencils through L2 (default 16);
+ *    launch, reading the displacement and stencils through L2 (default 32);
  *  - larger levels with at most split_max_n cells per axis: one launch per colour pass with
  *    a thread per (vertex, load case), each loading a z-layer of 9 neighbours before its
  *    FMAs (default 32);

@@ -378,7 +378,7 @@ __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
-constexpr int kClusterBlock = 64;
+constexpr int kClusterBlock = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kClusterBlock) k_coarse_gs_cluster(const T* __restrict__ st,

@@ -177,7 +177,7 @@ struct homo_ctx {
   // levels with at most gs_split_n one launch per colour with a thread per (vertex, case),
   // larger levels one launch per colour with a thread per vertex; gs_cluster: the largest
   // cluster the device launches (-1: none, per-colour launches everywhere)
-  int gs_fuse_n = 16, gs_split_n = 32, gs_cluster = -1;
+  int gs_fuse_n = 32, gs_split_n = 32, gs_cluster = -1;
   // levels with at most gs_res_n cells per axis (FP32 stencils, shared memory permitting)
   // keep each case's displacement resident in the clusters' shared memory instead;
   // gs_resident: the largest cluster of that form the device launches (-1: none)

@@ -39,7 +39,7 @@ def cuda(a):
 def test_settings_and_cluster_size(B):
     hom = B.Homogenization(16)
     resident_max_n, cluster_max_n, split_max_n, cluster, resident = hom.coarse_smoother()
-    assert (resident_max_n, cluster_max_n, split_max_n) == (16, 16, 32)
+    assert (resident_max_n, cluster_max_n, split_max_n) == (16, 32, 32)
     assert cluster in (4, 8, 16), cluster
     assert resident in (8, 16), resident     # 16^3 needs 8 CTAs of 64 vertices per colour
     hom.set_coarse_smoother(0, 0, 0)
@@ -53,9 +53,9 @@ def test_settings_and_cluster_size(B):
 @pytest.mark.parametrize("precision", ["fp32", "mixed"])
 @pytest.mark.parametrize("reverse", [False, True])
 def test_single_sweeps_bitwise_equal(B, precision, reverse):
-    """n = 64: levels 32, 16, 8, 4. At 32^3 an L2 cluster needs 16 CTAs with several
-    vertices per thread (the resident form falls back to it there); at 16^3 the resident
-    form runs 8 CTAs per case that exchange their updates, at 8^3 and 4^3 one CTA."""
+    """n = 64: levels 32, 16, 8, 4. At 32^3 an L2 cluster needs 16 CTAs of 256 threads
+    (the resident form falls back to it there); at 16^3 the resident form runs 8 CTAs per
+    case that exchange their updates, at 8^3 and 4^3 one CTA."""
     n = 64
     hom = B.Homogenization(n, precision=precision)
     hom.set_density(cuda(uniform_density(n, 900, 0.05, 1.0)))
@@ -88,7 +88,7 @@ def test_vcycle_bitwise_equal(B, precision):
     r = uniform_field(18 * n ** 3, 920, -1, 1).reshape(18, -1)
     r = cuda(r - r.mean(axis=1, keepdims=True))
     outs = []
-    for sizes in [(0, 0, 0), (0, 0, 1024), (0, 1024, 0), (1024, 1024, 0), (8, 16, 32), (16, 16, 32),
+    for sizes in [(0, 0, 0), (0, 0, 1024), (0, 1024, 0), (1024, 1024, 0), (8, 16, 32), (16, 32, 32),
                   (0, 32, 0), (16, 0, 64)]:
         hom.set_coarse_smoother(*sizes)
         z = torch.empty(18 * n ** 3, device="cuda")
@@ -103,7 +103,7 @@ def test_solve_and_CH_bitwise_equal(B):
     n = 32
     rho = cuda(smoothed_threshold_density(n, 0.3, 4))
     res = []
-    for sizes in [(0, 0, 0), (16, 16, 32)]:
+    for sizes in [(0, 0, 0), (16, 32, 32)]:
         hom = B.Homogenization(n)
         hom.set_coarse_smoother(*sizes)
         hom.set_density(rho)
