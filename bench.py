@@ -752,8 +752,12 @@ def run_ours(args, rank, world, local):
         hom.filter(2.0, loop.r, loop.rt)
         hom.set_density(loop.rt)
         choice, times = hom.autotune(retime=True)
+        csizes, ctimes = hom.autotune_coarse(retime=True)
         tuning = {"cases_per_thread": choice[0], "threads_per_block": choice[1],
-                  "ms_per_sweep": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times.items()}}
+                  "ms_per_sweep": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times.items()},
+                  "coarse_smoother": {"sizes": list(csizes),
+                                      "ms_per_level_phase_pair": {f"{n >> lev}^3": {f: round(v, 4) for f, v in row.items()}
+                                                                  for lev, row in ctimes.items()}}}
     net_info = None
     compare = None
     if args.warm_start != "previous" or args.compare_starts:
@@ -965,9 +969,12 @@ def run_batch(args, rank, world, local):
             c["hom"].filter(2.0, c["r"], c["rt"])
             c["hom"].set_density(c["rt"])
             choice, times = c["hom"].autotune()
+            csizes, ctimes = c["hom"].autotune_coarse()
             if times:
                 tuning[c["n"]] = {"cases_per_thread": choice[0], "threads_per_block": choice[1],
                                   "ms_per_sweep": {f"{k[0]}x{k[1]}": round(v, 4) for k, v in times.items()}}
+            if ctimes:
+                tuning.setdefault(c["n"], {})["coarse_smoother_sizes"] = list(csizes)
         torch.cuda.synchronize()
     it = {"k": 0, "cg": []}
 

@@ -408,6 +408,22 @@ int homo_set_coarse_smoother(homo_ctx* ctx, int resident_max_n, int cluster_max_
 int homo_coarse_smoother(const homo_ctx* ctx, int* resident_max_n, int* cluster_max_n, int* split_max_n,
                          int* cluster, int* resident_cluster);
 
+/* Autotuner of the coarse Gauss-Seidel forms. Times, on every smoothed coarse level of the
+ * context's own hierarchy, the two smoothing phases of a V-cycle (the level's sweep count
+ * from zero in colour order 0..7, then in order 7..0) in each form the level can take (the
+ * thread-per-vertex form everywhere, the thread-per-(vertex, case) form up to 128^3, the
+ * cluster forms up to 64^3 and where the device launches them), then sets the three sizes
+ * of homo_set_coarse_smoother (each 0 or a level size) whose forms give the smallest sum
+ * of those times, and caches them per (grid size, precision, sweep schedule) for the
+ * process; flags HOMO_TUNE_RETIME ignores the cache. Needs a density; uses the coarse
+ * levels' vectors, so call it between solves. The forms give bitwise the same iterates,
+ * so the choice changes only the time. Outputs (host, nullable): the chosen sizes; ms:
+ * 64 doubles, ms[4 l + k] the time of level l's two phases in form k (0 thread per
+ * vertex, 1 thread per (vertex, case), 2 cluster through L2, 3 resident cluster), -1 where
+ * not timed (all -1 when the choice came from the cache). (The paper has no counterpart.) */
+int homo_autotune_coarse(homo_ctx* ctx, int flags, int* resident_max_n, int* cluster_max_n, int* split_max_n,
+                         double* ms);
+
 /* One 8-colour block Gauss-Seidel sweep (Eq. 15-16) on level l, in place on u, colours
  * 0..7 (reverse = 0) or 7..0 (reverse = 1). f, u: device, 6-case layout on level l. */
 int homo_smooth(homo_ctx* ctx, int level, int reverse, const float* f, float* u);

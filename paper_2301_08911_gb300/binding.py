@@ -110,6 +110,7 @@ SIGNATURES = {
     "homo_autotune": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_int_p, _c_double_p]),
     "homo_set_coarse_smoother": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "homo_coarse_smoother": (ctypes.c_int, [_vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p, _c_int_p]),
+    "homo_autotune_coarse": (ctypes.c_int, [_vp, ctypes.c_int, _c_int_p, _c_int_p, _c_int_p, _c_double_p]),
     "homo_net_train_step": (ctypes.c_int, [_vp, ctypes.c_int, _vp, _vp, _c_double_p, ctypes.c_double,
                                            _c_double_p]),
     "homo_net_release": (ctypes.c_int, [_vp]),
@@ -366,6 +367,24 @@ class Homogenization:
         v = [ctypes.c_int() for _ in range(5)]
         self._check(self.lib.homo_coarse_smoother(self.h, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    COARSE_FORMS = ("vertex", "item", "cluster", "resident")
+
+    def autotune_coarse(self, retime: bool = False):
+        """Time the coarse Gauss-Seidel forms on this cell's levels and set the sizes whose
+        forms are fastest in total. Returns ((resident_max_n, cluster_max_n, split_max_n),
+        {level: {form: ms of the level's two smoothing phases}}) (no timings when the
+        choice came from the cache)."""
+        r, c, sp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        ms = (ctypes.c_double * 64)()
+        self._check(self.lib.homo_autotune_coarse(self.h, int(retime), ctypes.byref(r), ctypes.byref(c),
+                                                  ctypes.byref(sp), ms))
+        times = {}
+        for lev in range(16):
+            row = {f: ms[4 * lev + k] for k, f in enumerate(self.COARSE_FORMS) if ms[4 * lev + k] >= 0}
+            if row:
+                times[lev] = row
+        return (r.value, c.value, sp.value), times
 
     def autotune(self, retime: bool = False):
         """Time the fine Gauss-Seidel variants on this cell, select the fastest. Returns

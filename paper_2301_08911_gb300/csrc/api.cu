@@ -1,6 +1,7 @@
 // C ABI of the library (include/homo.h): context life cycle, the multigrid-preconditioned
 // CG driver for the 6 cell problems, C^H, sensitivities, filter and OC update.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1348,6 +1349,122 @@ int homo_set_coarse_smoother(homo_ctx* ctx, int resident_max_n, int cluster_max_
   ctx->gs_res_n = resident_max_n;
   ctx->gs_fuse_n = cluster_max_n;
   ctx->gs_split_n = split_max_n;
+  return HOMO_OK;
+}
+
+namespace {
+std::mutex g_coarse_tune_mu;
+// (grid size, precision, level-1 sweeps, sweep growth, levels) -> (resident, cluster, split)
+std::map<std::array<int, 5>, std::array<int, 3>> g_coarse_tune_cache;
+
+// The coarse Gauss-Seidel form smooth_level_sweeps picks for level l under sizes (r, c, s):
+// 0 vertex, 1 item, 2 cluster, 3 resident.
+int coarse_form(const homo_ctx* ctx, int l, int r, int c, int s) {
+  const homo::Level& lv = ctx->lev[l];
+  if (ctx->gs_resident > 0 && lv.n <= r && homo::coarse_resident_ok(lv, ctx->gs_resident)) return 3;
+  if (ctx->gs_cluster > 0 && lv.n <= c) return 2;
+  return lv.n <= s ? 1 : 0;
+}
+}  // namespace
+
+int homo_autotune_coarse(homo_ctx* ctx, int flags, int* resident_max_n, int* cluster_max_n, int* split_max_n,
+                         double* ms) {
+  if (!ctx) return HOMO_EINVAL;
+  if (!ctx->density_set) return set_err(ctx, HOMO_ESTATE, "homo_autotune_coarse needs a density");
+  constexpr int kForms = 4;
+  static const int kSizes[kForms][3] = {{0, 0, 0}, {0, 0, 1024}, {0, 1024, 0}, {1024, 1024, 0}};
+  if (ms)
+    for (int k = 0; k < kMaxLevels * kForms; ++k) ms[k] = -1.0;
+  const std::array<int, 5> key = {ctx->n, ctx->opts.precision, ctx->opts.coarse_sweeps, ctx->opts.sweep_growth,
+                                  ctx->nlev};
+  std::array<int, 3> best = {-1, -1, -1};
+  if (!(flags & HOMO_TUNE_RETIME)) {
+    std::lock_guard<std::mutex> lk(g_coarse_tune_mu);
+    auto it = g_coarse_tune_cache.find(key);
+    if (it != g_coarse_tune_cache.end()) best = it->second;
+  }
+  if (best[0] < 0) {
+    // time each coarse level's two smoothing phases of a V-cycle (the first from zero, the
+    // second in reverse colour order) in every form the level can take, on the level's own
+    // stencils; the level vectors are free between solves
+    RET(ensure_hierarchy(ctx));
+    const int last = ctx->nlev - 1;   // the coarsest level is solved, not smoothed
+    double t[kMaxLevels][kForms];
+    for (auto& row : t)
+      for (double& v : row) v = -1.0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      return set_err(ctx, HOMO_ECUDA, "homo_autotune_coarse: cudaEventCreate failed");
+    }
+    const int save_r = ctx->gs_res_n, save_c = ctx->gs_fuse_n, save_s = ctx->gs_split_n;
+    int rc = HOMO_OK;
+    for (int l = 1; l < last && rc == HOMO_OK; ++l) {
+      homo::Level& lv = ctx->lev[l];
+      const int sw = level_sweeps(ctx, l);
+      if (launch_fill_hash(lv.b, kPlanes * lv.N, 0x70e50000u + static_cast<unsigned>(l), ctx->stream) != cudaSuccess) {
+        rc = HOMO_ECUDA;
+        break;
+      }
+      for (int k = 0; k < kForms && rc == HOMO_OK; ++k) {
+        // candidates: the per-colour item form up to 128^3, the cluster forms up to 64^3
+        // (one cluster of at most 16 CTAs per load case), the resident form where it fits
+        if ((k == 1 && lv.n > 128) || (k >= 2 && lv.n > 64)) continue;
+        ctx->gs_res_n = kSizes[k][0];
+        ctx->gs_fuse_n = kSizes[k][1];
+        ctx->gs_split_n = kSizes[k][2];
+        if (coarse_form(ctx, l, ctx->gs_res_n, ctx->gs_fuse_n, ctx->gs_split_n) != k) continue;
+        const int reps = lv.n <= 32 ? 4 : 1;
+        for (int rep = -1; rep < reps && rc == HOMO_OK; ++rep) {   // rep -1: warm-up
+          if (rep == 0 && cudaEventRecord(a, ctx->stream) != cudaSuccess) rc = HOMO_ECUDA;
+          if (rc == HOMO_OK) rc = smooth_level_sweeps(ctx, l, false, lv.b, lv.x, sw, true);
+          if (rc == HOMO_OK) rc = smooth_level_sweeps(ctx, l, true, lv.b, lv.x, sw);
+        }
+        if (rc != HOMO_OK) break;
+        float el = 0.f;
+        if (cudaEventRecord(b, ctx->stream) != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+            cudaEventElapsedTime(&el, a, b) != cudaSuccess) {
+          rc = HOMO_ECUDA;
+          break;
+        }
+        t[l][k] = el / reps;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->gs_res_n = save_r;
+    ctx->gs_fuse_n = save_c;
+    ctx->gs_split_n = save_s;
+    if (rc != HOMO_OK) return rc == HOMO_ECUDA ? set_err(ctx, rc, "homo_autotune_coarse: timing failed") : rc;
+    // the sizes (each 0 or a level size) whose forms give the smallest total phase time;
+    // ascending, so that of equivalent sizes the smallest is reported
+    std::vector<int> cand = {0};
+    for (int l = last - 1; l >= 1; --l) cand.push_back(ctx->lev[l].n);
+    double best_t = -1.0;
+    for (int r : cand)
+      for (int c : cand)
+        for (int sp : cand) {
+          double tot = 0.0;
+          for (int l = 1; l < last && tot >= 0.0; ++l) {
+            const double v = t[l][coarse_form(ctx, l, r, c, sp)];
+            tot = v < 0.0 ? -1.0 : tot + v;
+          }
+          if (tot >= 0.0 && (best_t < 0.0 || tot < best_t)) {
+            best_t = tot;
+            best = {r, c, sp};
+          }
+        }
+    if (best[0] < 0) return set_err(ctx, HOMO_ECUDA, "homo_autotune_coarse: no form timed on every level");
+    if (ms)
+      for (int l = 0; l < kMaxLevels; ++l)
+        for (int k = 0; k < kForms; ++k) ms[l * kForms + k] = t[l][k];
+    std::lock_guard<std::mutex> lk(g_coarse_tune_mu);
+    g_coarse_tune_cache[key] = best;
+  }
+  RET(homo_set_coarse_smoother(ctx, best[0], best[1], best[2]));
+  if (resident_max_n) *resident_max_n = best[0];
+  if (cluster_max_n) *cluster_max_n = best[1];
+  if (split_max_n) *split_max_n = best[2];
   return HOMO_OK;
 }
 

@@ -123,3 +123,4 @@ def test_tuning_argument_checks(lib):
     assert lib.homo_autotune(None, 0, None, None, None) == binding.HOMO_EINVAL
     assert lib.homo_set_coarse_smoother(None, 16, 16, 32) == binding.HOMO_EINVAL
     assert lib.homo_coarse_smoother(None, None, None, None, None, None) == binding.HOMO_EINVAL
+    assert lib.homo_autotune_coarse(None, 0, None, None, None, None) == binding.HOMO_EINVAL

@@ -117,3 +117,58 @@ def test_solve_and_CH_bitwise_equal(B):
     assert res[0][0] == res[1][0]
     assert np.array_equal(res[0][1], res[1][1])
     assert torch.equal(res[0][2], res[1][2])
+
+
+def _form(level_n, sizes, timed, cluster):
+    """The form the library picks for a level of size level_n under sizes (resident,
+    cluster, split): the resident form where it was timed (timed exactly where it fits),
+    the L2 cluster form where the device launches clusters, else item or vertex."""
+    r, c, s = sizes
+    if level_n <= r and "resident" in timed:
+        return "resident"
+    if cluster > 0 and level_n <= c:
+        return "cluster"
+    return "item" if level_n <= s else "vertex"
+
+
+def test_autotune_coarse_picks_the_fastest_sizes(B):
+    import itertools
+    n = 64
+    hom = B.Homogenization(n)
+    hom.set_density(cuda(smoothed_threshold_density(n, 0.3, 5)))
+    r = uniform_field(18 * n ** 3, 930, -1, 1).reshape(18, -1)
+    r = cuda(r - r.mean(axis=1, keepdims=True))
+    z0 = torch.empty(18 * n ** 3, device="cuda")
+    hom.vcycle(r, z0)
+    sizes, times = hom.autotune_coarse(retime=True)
+    cluster = hom.coarse_smoother()[3]
+    smoothed = list(range(1, hom.num_levels - 1))          # levels 32, 16, 8 (4 is solved)
+    assert sorted(times) == smoothed
+    assert all("vertex" in times[lev] for lev in smoothed)
+    level_n = {lev: n >> lev for lev in smoothed}
+    cand = [0] + [level_n[lev] for lev in smoothed]
+    assert all(x in cand for x in sizes)
+    assert hom.coarse_smoother()[:3] == sizes
+
+    def total(sz):
+        t = 0.0
+        for lev in smoothed:
+            f = _form(level_n[lev], sz, times[lev], cluster)
+            if f not in times[lev]:
+                return None
+            t += times[lev][f]
+        return t
+
+    best = total(sizes)
+    assert best is not None
+    for sz in itertools.product(cand, repeat=3):
+        other = total(sz)
+        assert other is None or best <= other, (sizes, best, sz, other)
+    # a second call takes the cached choice without timing
+    again, t2 = hom.autotune_coarse()
+    assert again == sizes and t2 == {}
+    # the tuned forms give bitwise the V-cycle of the default ones
+    z1 = torch.empty_like(z0)
+    hom.vcycle(r, z1)
+    torch.cuda.synchronize()
+    assert torch.equal(z0, z1)
