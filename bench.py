@@ -424,9 +424,10 @@ def coarse_forms(hom, n, stream, dev):
 
 # ------------------------------------------------------------------ reference arm
 def run_reference(args, rank, world):
-    """The oracle as it stands, timed on the host cores for the same workload: each step is
-    one oracle optimisation iteration of a 32^3 sample of the workload's generator, scaled
-    by element count to the workload's n^3 (a lower bound)."""
+    """The oracle as it stands, timed on one host core for the same workload: each step is
+    one oracle optimisation iteration of a --sample-n^3 sample (default 16^3, sparse LU) of
+    the workload's generator, scaled by element count to the workload's n^3 (a lower
+    bound: the oracle's cost grows faster than the element count)."""
     if rank != 0:
         return 0
     reps = args.warmup + args.steps
