@@ -182,6 +182,36 @@ def test_certified_cg_matches_direct_solves(n, kind):
             assert e @ (K @ e) <= 1e-18 + 1e-12 * C_lu[i, i], (method, i)
 
 
+def test_multisweep_vcycle_is_symmetric_and_contracts_faster():
+    """The oracle's V-cycle with several sweeps per level (the GPU library's schedule): with
+    colours 0..7 before and 7..0 after the coarse correction, M is symmetric and positive on
+    mean-free vectors (a wrong colour order or a missing sweep breaks the symmetry), and
+    more smoothing makes the error propagation I - M K contract more in the energy norm."""
+    from oracle.pcg import MultigridPreconditioner, _project
+    n = 16                                                     # levels 16, 8, 4
+    rho = uniform_density(n, 900, 0.05, 1.0).astype(np.float64)
+    h = 1.0 / n
+    K = oracle.assemble_K(n, oracle.simp_modulus(rho), oracle.ke_hex8(1.0, 0.3, h)) / h
+    rng = np.random.default_rng(5)
+    x = _project(rng.standard_normal((3 * n ** 3, 2)))
+    M13 = MultigridPreconditioner(K, n, sweeps=[1, 3])
+    Mx = M13(x)
+    a, b = x[:, 0] @ Mx[:, 1], x[:, 1] @ Mx[:, 0]
+    assert abs(a - b) <= 1e-12 * np.sqrt((x[:, 0] @ Mx[:, 0]) * (x[:, 1] @ Mx[:, 1]))
+    assert (x * Mx).sum(axis=0).min() > 0
+    with pytest.raises(ValueError):
+        MultigridPreconditioner(K, n, sweeps=[1])
+
+    def energy_contraction(M):
+        e = x - _project(M(K @ x))                             # (I - M K) x on the range of K
+        return np.sqrt(np.sum(e * (K @ e)) / np.sum(x * (K @ x)))
+
+    c11 = energy_contraction(MultigridPreconditioner(K, n))
+    c13 = energy_contraction(M13)
+    c33 = energy_contraction(MultigridPreconditioner(K, n, sweeps=[3, 3]))
+    assert c33 < c13 < c11 < 1.0, (c11, c13, c33)
+
+
 def test_certified_cg_full_solid_and_laminate():
     """Closed forms through the iterative oracle: the full solid returns D with u = 0, and a
     1-D laminate returns the Backus tensor, at 24^3 where the direct solve is slow."""
