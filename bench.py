@@ -232,8 +232,9 @@ def algorithmic_work(kc: str, n: int, sweeps: int = 1):
         return 220 * N, STENCIL_FLOP * N
     if kc == "true_residual":    # f - K (u + ulo): E 4N + u 72N + ulo 72N + f 72N + out 72N
         return 292 * N, STENCIL_FLOP * N
-    if kc == "element":          # u 72N + E/rho 8N (+ out 4N); 6 x 576 + 21 x 24 FMA per element
-        return 80 * N, (6 * 576 + 21 * 24) * 2 * N
+    if kc == "element":          # u and ulo 144N, E (C^H) or rho and the output (sensitivity) 4N / 8N:
+        # the class holds one launch of each, 150N on average; 6 x 576 + 21 x 24 FMA per element
+        return 150 * N, (6 * 576 + 21 * 24) * 2 * N
     return None, None
 
 
