@@ -48,6 +48,18 @@ def _block_inverses(K: sp.csr_matrix, verts: np.ndarray) -> np.ndarray:
     return np.linalg.inv(S)
 
 
+def pseudo_inverse(A: np.ndarray) -> np.ndarray:
+    """Moore-Penrose inverse of a periodic stiffness operator (dense, symmetric), whose null
+    space is exactly the three rigid translations (Sec. 4.2 "Singular stiffness matrices"):
+    the eigendecomposition with the three eigenpairs of smallest magnitude dropped. (A
+    relative cutoff is not used: in FP64 the translation eigenvalues come out near 1e-14 of
+    the largest, which a default cutoff of 1e-15 would invert.)"""
+    w, V = np.linalg.eigh(A)
+    keep = np.argsort(np.abs(w))[3:]
+    Vk = V[:, keep]
+    return (Vk / w[keep]) @ Vk.T
+
+
 def _project(z: np.ndarray) -> np.ndarray:
     """Remove the rigid translations: subtract each component's mean, per column."""
     out = z.reshape(-1, 3, z.shape[1])
@@ -91,7 +103,7 @@ class MultigridPreconditioner:
         A = K.tocsr()
         for l, nl in enumerate(sizes):
             if l == len(sizes) - 1:
-                self.coarsest = np.linalg.pinv(A.toarray(), hermitian=True)
+                self.coarsest = pseudo_inverse(A.toarray())
                 break
             self.levels.append(_Level(A, nl))
             P = prolongation(sizes[l + 1])

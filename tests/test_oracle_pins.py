@@ -182,6 +182,34 @@ def test_certified_cg_matches_direct_solves(n, kind):
             assert e @ (K @ e) <= 1e-18 + 1e-12 * C_lu[i, i], (method, i)
 
 
+def test_coarsest_pseudo_inverse_satisfies_its_definition():
+    """The V-cycle's coarsest solve is the Moore-Penrose inverse G of the coarsest Galerkin
+    operator A: A G A = A, G A G = G, G symmetric, and G annihilates the three rigid
+    translations that span A's null space (Sec. 4.2). A relative-cutoff pseudo-inverse
+    keeps A's translation eigenvalues (about 1e-14 of the largest in FP64) and fails the
+    first identity by 0.4 % on this operator."""
+    from oracle.mg import level_sizes, prolongation
+    from oracle.pcg import pseudo_inverse
+    n = 32
+    rho = uniform_density(n, 940, 0.05, 1.0).astype(np.float64)
+    h = 1.0 / n
+    A = oracle.assemble_K(n, oracle.simp_modulus(rho), oracle.ke_hex8(1.0, 0.3, h)) / h
+    for nl in level_sizes(n)[1:]:
+        P = prolongation(nl)
+        A = (P.T @ A @ P).tocsr()
+    A = A.toarray()                                            # 4^3 vertices, 192 unknowns
+    G = pseudo_inverse(A)
+    T = np.zeros((A.shape[0], 3))
+    for c in range(3):
+        T[c::3, c] = 1.0
+    nA, nG = np.linalg.norm(A), np.linalg.norm(G)
+    assert np.linalg.norm(A @ G @ A - A) <= 1e-12 * nA
+    assert np.linalg.norm(G @ A @ G - G) <= 1e-12 * nG
+    assert np.abs(G - G.T).max() <= 1e-13 * np.abs(G).max()
+    assert np.abs(G @ T).max() <= 1e-12 * np.abs(G).max()
+    assert np.linalg.norm(A @ np.linalg.pinv(A, hermitian=True) @ A - A) > 1e-4 * nA
+
+
 def test_multisweep_vcycle_is_symmetric_and_contracts_faster():
     """The oracle's V-cycle with several sweeps per level (the GPU library's schedule): with
     colours 0..7 before and 7..0 after the coarse correction, M is symmetric and positive on
